@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 cooperative conjugate gradient (cCG) solver.
+
+One step = one complete FP64 cCG solve (initial residual, iterations to
+relative residual 1e-10, true-residual check, copy-out) of the dense SPD
+system A x = b with A the exponential kernel exp(-|z_i - z_j| / 0.2) on 8192
+points uniform in [0, 1]^3 (seed 1) plus 1e-2 I, b ~ N(0, 1), x0 = 0, p = 8
+agents.  The metric is solves/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--p P] [--impl ours|reference]
+
+N > 1 runs independent replicas (one solve per rank per step; the method has
+no cross-GPU data path in this build), launched by torchrun.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(bounded sample of iterations, scaled to a full solve).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 8192
+TOL = 1e-10
+WORKLOAD = ("plain FP64 cCG: A = exp(-|z_i-z_j|/0.2) + 1e-2 I on n=8192 points U[0,1]^3 "
+            "(seed 1), b ~ N(0,1), x0 = 0, tol 1e-10 relative")
+METRIC = "solves/s at relres 1e-10 (FP64 cCG)"
+GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n):
+    from paper_1204_0069_gb300 import workloads as wl
+    return wl.exp_kernel(n, seed=1, length=0.2, nugget=1e-2)
+
+
+def oracle_full_iterations(n, p):
+    try:
+        rows = json.load(open(GOLDEN_ITERS))["rows"]
+    except (OSError, ValueError, KeyError):
+        return None
+    for r in rows:
+        if r["n"] == n and r["p"] == p and r["workload"].startswith("exp_kernel"):
+            return int(r["iterations"])
+    return None
+
+
+def cpu_sample(A, b, p, target_s):
+    """Time a bounded sample of oracle iterations on all host cores and scale
+    it to one full solve.  Returns (solves_per_s, cores, sample_text)."""
+    import oracle
+    n = b.shape[0]
+    cores = os.cpu_count() or 1
+    X0 = oracle.initial_block(n, p, None, 1.0, 0)
+    t0 = time.perf_counter()
+    oracle.ccg(A, b, X0, 1e-300, 2, residual_replacement=False, nthreads=cores)
+    t2 = time.perf_counter() - t0          # init + 2 iterations + residual check
+    m = max(2, int(target_s / max(t2 / 2.0, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.ccg(A, b, X0, 1e-300, m, residual_replacement=False, nthreads=cores)
+    tm = time.perf_counter() - t0
+    full = oracle_full_iterations(n, p)
+    per_it = (tm - t2) / max(m - 2, 1)
+    fixed = max(t2 - 2 * per_it, 0.0)      # init A X_0 + final true residual
+    if full is None:
+        full = m
+        note = "full iteration count unknown: scaled to the sample length"
+    else:
+        note = f"scaled to the oracle's full solve of {full} iterations"
+    t_solve = fixed + per_it * full
+    return 1.0 / t_solve, cores, (f"first {m} oracle iterations (n={n}, p={p}, {tm:.1f} s on "
+                                  f"{cores} threads), {note}")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def solve_flops(n, p, iters, checks, replacements):
+    """Algorithmic FP64 flops of one solve (Table 1 counts x 2 for multiply-add):
+    A X_0 (2 n^2 p), per iteration A D (2 n^2 p) + six n x p x p products
+    (12 n p^2), one true-residual product (2 n^2) per check, and one A X per
+    residual replacement."""
+    return (2.0 * n * n * p + iters * (2.0 * n * n * p + 12.0 * n * p * p)
+            + checks * 2.0 * n * n + replacements * 2.0 * n * n * p)
+
+
+def solve_bytes(n, p, iters, checks, replacements):
+    """Algorithmic HBM bytes: A (8 n^2) once per block product plus the
+    n x p blocks each pass touches (about 10 n p doubles per iteration)."""
+    passes = 1 + iters + checks + replacements
+    return 8.0 * n * n * passes + iters * 80.0 * n * p
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    A, b = workload(args.n)
+    per_step = max(2.0, args.cpu_seconds / max(args.steps, 1))
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        v, cores, sample = cpu_sample(A, b, args.p, per_step)
+        if i >= args.warmup:
+            vals.append(v)
+            info = (cores, sample)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": args.n, "p": args.p, "tol": TOL,
+                       "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": info[0],
+                             "kind": "oracle", "sample": info[1]},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        ge.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1204_0069_gb300 import ccg
+
+    n, p = args.n, args.p
+    A, b = workload(n)
+    dev = torch.device("cuda", local)
+    dA = torch.from_numpy(A).to(dev)
+    db = torch.from_numpy(b).to(dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    solver = ccg.Solver(device=local, stream=stream.cuda_stream)
+    maxit = 20 * n
+
+    def step():
+        r = solver.solve(dA, db, x, p=p, tol=TOL, maxit=maxit)
+        if r.status != 0:
+            raise RuntimeError(f"solve failed: {r}")
+        return r
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    results = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1000.0
+    if dist is not None:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps / elapsed
+    kernel_ms = [r.device_ms for r in results]
+    r0 = results[-1]
+
+    # A.D block product alone (same device code as each iteration's A-pass)
+    V = torch.randn(n, p, dtype=torch.float64, device=dev)
+    W = torch.empty(n, p, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        solver.block_product(dA, V, W, want_grams=True)
+    bp = [solver.block_product(dA, V, W, want_grams=True)[3] for _ in range(10)]
+    bp_ms = statistics.mean(bp)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.from_numpy(A).pin_memory()
+        hb = torch.from_numpy(b).pin_memory()
+        hx = torch.zeros(n, dtype=torch.float64).pin_memory()
+        solver.solve(hA, hb, hx, p=p, tol=TOL, maxit=maxit)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            r = solver.solve(hA, hb, hx, p=p, tol=TOL, maxit=maxit)
+            if r.status != 0:
+                raise RuntimeError(f"e2e solve failed: {r}")
+        f1.record(stream)
+        torch.cuda.synchronize()
+        et = f0.elapsed_time(f1) / 1000.0
+        if dist is not None:
+            t = torch.tensor([et], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        e2e = {"value": world * args.steps / et, "unit": "solves/s",
+               "h2d_bytes_per_step": int(A.nbytes + b.nbytes),
+               "d2h_bytes_per_step": int(8 * n + 192)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_sample(A, b, p, args.cpu_seconds)
+        cpu = {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+               "sample": sample}
+
+    if rank == 0:
+        checks = 1 + r0.replacements
+        fl = solve_flops(n, p, r0.iterations, checks, r0.replacements)
+        by = solve_bytes(n, p, r0.iterations, checks, r0.replacements)
+        kms = statistics.mean(kernel_ms)
+        peaks = measured_peaks()
+        fp64_peak = 1.25  # TFLOP/s: nominal GB300 FP64 rate (no measured FP64 figure)
+        achieved = fl / (kms / 1e3) / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "p": p, "tol": TOL,
+                       "l2": "inputs larger than L2 (A = 512 MiB FP64 > 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "iterations": r0.iterations, "relres_true": r0.relres_true,
+            "latency_ms": {"p50": float(np.percentile(kernel_ms, 50)),
+                           "p99": float(np.percentile(kernel_ms, 99))},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                         "kernel": "fp64_kernel<8,true> (persistent solve)",
+                         "peak_note": "nominal FP64 rate (FP64 pipe bound)"},
+            "apass": {"ms": bp_ms, "gbs": 8.0 * n * n / (bp_ms / 1e3) / 1e9,
+                      "tflops": 2.0 * n * n * p / (bp_ms / 1e3) / 1e12,
+                      "hbm_peak_gbs": peaks.get("hbm_gbs")},
+            "algorithmic": {"flops_per_solve": fl, "bytes_per_solve": by},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+        }
+        if e2e is not None:
+            line["e2e"] = e2e
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

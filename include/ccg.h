@@ -1,0 +1,167 @@
+/*
+ * ccg.h -- C ABI of the GB300 cooperative conjugate gradient (cCG) solver.
+ *
+ * Method: Bhaya, Bliman, Niedu, Pazos, "A cooperative conjugate gradient
+ * method for linear systems permitting multithread implementation of low
+ * complexity", arXiv:1204.0069.  Problem statement: solve A x = b for a dense
+ * symmetric positive definite A (Sec. 2, Eq. "equa"), i.e. minimise
+ * f(x) = x'Ax/2 - b'x, with p cooperating agents (Sec. 3.2, Algorithm 2),
+ * the rank-deficiency deflation of Algorithm 3 and the stopping rule of
+ * Algorithm 4.
+ *
+ * Conventions used by every entry point:
+ *   - All matrices are row-major.  A is n x n with leading dimension lda
+ *     (elements, lda >= n).  Blocks of agents (X0, X_out, V, W) are n x p
+ *     row-major with leading dimension p: element (i, j) -- row i, agent j --
+ *     is at [i*p + j].
+ *   - Residues are gradients, r = A x - b (Sec. 2); only norms leave the
+ *     library, so the sign is internal.
+ *   - Pointers may be device memory (e.g. torch CUDA tensors) or host memory.
+ *     Host buffers are copied to handle-owned device buffers inside the call
+ *     and results are copied back; device buffers are used in place.  The
+ *     caller keeps ownership of every buffer it passes; the library only
+ *     borrows them for the duration of the call and never writes A or b.
+ *   - Work is ordered on the handle's stream (ccg_config.stream, NULL = the
+ *     legacy default stream).  Every solve returns after its results are
+ *     available on the host (it synchronises that stream at the end).
+ *   - Return values are status codes (ccg_status).  Nothing is thrown across
+ *     the ABI.  After any error other than CCG_ERR_CUDA the handle stays
+ *     usable.  A handle must not be used by two host threads at once.
+ *   - Device pointers must be 8-byte aligned (16-byte aligned A with an even
+ *     lda selects the vectorised A stream).
+ */
+#ifndef CCG_H
+#define CCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CCG_MAX_AGENTS 32
+
+/* Opaque solver handle. */
+typedef struct ccg_handle_s ccg_handle;
+
+typedef enum {
+    CCG_OK = 0,              /* converged: true relative residual <= tol     */
+    CCG_NOT_CONVERGED = 1,   /* warning: maxit reached; x_out = best agent   */
+    CCG_ERR_INVALID = -1,    /* bad argument (sizes, tol, NULL, alignment)   */
+    CCG_ERR_NOT_SPD = -2,    /* A found not positive definite (Gram pivot)   */
+    CCG_ERR_NUMERICAL = -3,  /* NaN or Inf appeared                          */
+    CCG_ERR_OOM = -4,        /* device allocation failed                     */
+    CCG_ERR_TIMEOUT = -5,    /* an in-kernel grid barrier gave up waiting    */
+    CCG_ERR_CUDA = -6        /* CUDA runtime error                           */
+} ccg_status;
+
+typedef enum {
+    CCG_FP64 = 0             /* every operation in FP64                      */
+} ccg_precision;
+
+typedef struct {
+    int device;                 /* CUDA device ordinal                       */
+    void* stream;               /* cudaStream_t; NULL = legacy default       */
+    int precision;              /* ccg_precision                             */
+    double rank_tol;            /* deflation threshold on the scaled Cholesky
+                                   pivots of D'AD (Algorithm 3); default 1e-12 */
+    double x0_spread;           /* initial-block spread for ccg_solve; 1.0   */
+    uint64_t seed;              /* initial-block seed for ccg_solve; 0       */
+    int residual_replacement;   /* 1: if the true residual at exit is above
+                                   tol, restart from R = A X - b 1' (default)*/
+    double barrier_timeout_ms;  /* in-kernel barrier wait limit; 10000 ms    */
+    int max_ctas;               /* 0 = one CTA per SM; else an upper bound   */
+} ccg_config;
+
+typedef struct {
+    int status;           /* ccg_status of the solve                          */
+    int iterations;       /* cCG iterations = A*D_k products in the loop      */
+    int agent;            /* original index of the agent returned in x_out   */
+    int p_final;          /* agents still active at exit (Algorithm 3)        */
+    int replacements;     /* residual replacements performed                  */
+    int drops;            /* agents removed by the rank test                  */
+    double relres_true;   /* ||b - A x_out|| / ||b|| computed in FP64         */
+    double relres_recur;  /* min_j ||R e_j|| / ||b|| from the recurrence      */
+    float device_ms;      /* device time of the solve kernel(s)               */
+    int ctas;             /* CTAs of the persistent launch                    */
+} ccg_result;
+
+/* Fill *cfg with the defaults listed above. */
+void ccg_config_init(ccg_config* cfg);
+
+/* Create a solver handle bound to cfg->device and cfg->stream (NULL cfg =
+ * defaults).  The handle owns a growable device workspace, freed by
+ * ccg_destroy.  Returns CCG_ERR_INVALID on a bad device, CCG_ERR_CUDA if the
+ * device cannot be initialised. */
+int ccg_create(ccg_handle** out_handle, const ccg_config* cfg);
+
+/* Release the handle and its workspace.  NULL-safe. */
+int ccg_destroy(ccg_handle* handle);
+
+/*
+ * Solve A x = b with p agents (Algorithm 2 with the deflation of Algorithm 3).
+ *
+ *   n, A, lda : system matrix (SPD; symmetry is assumed, not checked).
+ *   b         : right-hand side, n values.
+ *   x0        : initial guess (n values) or NULL for zeros.  The agents'
+ *               initial block is X_0 e_0 = x0 and, for j >= 1,
+ *               X_0 e_j = x0 + x0_spread * u_j, where u_j(i) is uniform in
+ *               [-1, 1) from SplitMix64 at counter j*n + i under cfg seed
+ *               (top 53 bits).  The paper draws every agent's start at
+ *               random (Sec. 5); identical starts would collapse to CG.
+ *   p         : agents, 1 <= p <= min(n, 32).
+ *   tol       : relative tolerance > 0.  The loop stops when
+ *               min_j ||R_k e_j|| <= tol ||b|| (Algorithm 4, relative), and
+ *               the solve reports CCG_OK only if the true residual of the
+ *               returned agent, ||b - A x||/||b|| in FP64, is <= tol.
+ *   maxit     : maximum cCG iterations (>= 0).
+ *   x_out     : n values; receives the agent with the smallest residual.
+ *   res       : optional result record (host memory).
+ * Errors: CCG_ERR_INVALID (n < 1, p out of range, tol <= 0, maxit < 0,
+ * lda < n, NULL pointer), CCG_ERR_NOT_SPD, CCG_ERR_NUMERICAL, CCG_ERR_OOM,
+ * CCG_ERR_TIMEOUT, CCG_ERR_CUDA.  b = 0 returns x = 0 after 0 iterations.
+ */
+int ccg_solve(ccg_handle* handle, int64_t n, const double* A, int64_t lda,
+              const double* b, const double* x0, int p, double tol, int maxit,
+              double* x_out, ccg_result* res);
+
+/*
+ * As ccg_solve, with the initial block given explicitly (Algorithm 2, "choose
+ * X_0"): X0 is n x p row-major.  If X_out is not NULL it receives the final
+ * block (n x p row-major): column j holds agent j's last iterate (for an
+ * agent removed by the rank test, its iterate when it was removed).
+ */
+int ccg_solve_block(ccg_handle* handle, int64_t n, const double* A, int64_t lda,
+                    const double* b, const double* X0, int p, double tol,
+                    int maxit, double* x_out, double* X_out, ccg_result* res);
+
+/*
+ * One block product of Table 1, rows 1-3, with the same device code the
+ * solver runs each iteration: W = A V (n x q), and, if M / G are not NULL,
+ * the q x q Grams M = V' W (symmetrised, (M + M')/2) and G = U' V (U given,
+ * n x q, may equal V).  V, U, W are n x q row-major; M, G are q x q
+ * row-major.  1 <= q <= 32.  Errors as for ccg_solve.
+ */
+int ccg_block_product(ccg_handle* handle, int64_t n, const double* A, int64_t lda,
+                      const double* V, const double* U, int q, double* W,
+                      double* M, double* G, float* device_ms);
+
+/*
+ * Self-test of the in-kernel grid barrier's wait limit: launches the
+ * persistent kernel with a barrier that expects one more CTA than the grid
+ * holds, so every wait gives up after timeout_ms and the kernel returns.
+ * Returns CCG_ERR_TIMEOUT when the limit works (the handle stays usable).
+ */
+int ccg_selftest_barrier_timeout(ccg_handle* handle, double timeout_ms);
+
+/* Name of a status code ("CCG_OK", ...). */
+const char* ccg_status_string(int status);
+
+/* Library version string. */
+const char* ccg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCG_H */

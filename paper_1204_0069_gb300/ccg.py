@@ -1,0 +1,209 @@
+"""ctypes binding of the C ABI in ``include/ccg.h`` (libccg.so).
+
+Argument marshalling only: every step of a solve runs in the CUDA kernels of
+the library.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they
+must be C-contiguous float64.  There is no fallback: if ``libccg.so`` has not
+been built, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libccg.so")
+
+STATUS = {0: "CCG_OK", 1: "CCG_NOT_CONVERGED", -1: "CCG_ERR_INVALID", -2: "CCG_ERR_NOT_SPD",
+          -3: "CCG_ERR_NUMERICAL", -4: "CCG_ERR_OOM", -5: "CCG_ERR_TIMEOUT", -6: "CCG_ERR_CUDA"}
+OK, NOT_CONVERGED = 0, 1
+EXPORTED = ["ccg_config_init", "ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
+            "ccg_block_product", "ccg_selftest_barrier_timeout", "ccg_status_string",
+            "ccg_version"]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("precision", ctypes.c_int), ("rank_tol", ctypes.c_double),
+                ("x0_spread", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("residual_replacement", ctypes.c_int),
+                ("barrier_timeout_ms", ctypes.c_double), ("max_ctas", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("agent", ctypes.c_int), ("p_final", ctypes.c_int),
+                ("replacements", ctypes.c_int), ("drops", ctypes.c_int),
+                ("relres_true", ctypes.c_double), ("relres_recur", ctypes.c_double),
+                ("device_ms", ctypes.c_float), ("ctas", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = STATUS.get(self.status, str(self.status))
+        return d
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+
+def lib():
+    """Load libccg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libccg.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.ccg_config_init.argtypes = [ctypes.POINTER(Config)]
+        L.ccg_config_init.restype = None
+        L.ccg_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(Config)]
+        L.ccg_destroy.argtypes = [_VP]
+        L.ccg_solve.argtypes = [_VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_int, _VP, ctypes.POINTER(Result)]
+        L.ccg_solve_block.argtypes = [_VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, _VP, _VP,
+                                      ctypes.POINTER(Result)]
+        L.ccg_block_product.argtypes = [_VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_int, _VP, _VP,
+                                        _VP, ctypes.POINTER(ctypes.c_float)]
+        L.ccg_selftest_barrier_timeout.argtypes = [_VP, ctypes.c_double]
+        L.ccg_status_string.argtypes = [ctypes.c_int]
+        L.ccg_status_string.restype = ctypes.c_char_p
+        L.ccg_version.argtypes = []
+        L.ccg_version.restype = ctypes.c_char_p
+        for name in ["ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
+                     "ccg_block_product", "ccg_selftest_barrier_timeout"]:
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Data pointer of a contiguous float64 torch tensor / numpy array (or None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("arrays must be C-contiguous float64")
+        return a.ctypes.data
+    import torch  # local: torch is only needed for tensor arguments
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _current_stream(device: int):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device).cuda_stream
+    except Exception:  # pragma: no cover - torch without CUDA
+        pass
+    return None
+
+
+@dataclass
+class SolveResult:
+    status: int
+    status_name: str
+    iterations: int
+    agent: int
+    p_final: int
+    replacements: int
+    drops: int
+    relres_true: float
+    relres_recur: float
+    device_ms: float
+    ctas: int
+
+
+class Solver:
+    """A solver handle (``ccg_create``) bound to one device and stream."""
+
+    def __init__(self, device: int = 0, stream=None, rank_tol: float = 1e-12,
+                 x0_spread: float = 1.0, seed: int = 0, residual_replacement: bool = True,
+                 barrier_timeout_ms: float = 10000.0, max_ctas: int = 0):
+        L = lib()
+        cfg = Config()
+        L.ccg_config_init(ctypes.byref(cfg))
+        cfg.device = device
+        cfg.stream = stream if stream is not None else _current_stream(device)
+        cfg.rank_tol = rank_tol
+        cfg.x0_spread = x0_spread
+        cfg.seed = seed & (2**64 - 1)
+        cfg.residual_replacement = int(bool(residual_replacement))
+        cfg.barrier_timeout_ms = barrier_timeout_ms
+        cfg.max_ctas = max_ctas
+        h = _VP()
+        rc = L.ccg_create(ctypes.byref(h), ctypes.byref(cfg))
+        if rc != 0:
+            raise RuntimeError(f"ccg_create failed: {STATUS.get(rc, rc)}")
+        self._h = h
+        self._lib = L
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ccg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _res(r: Result) -> SolveResult:
+        d = r.as_dict()
+        return SolveResult(**{k: d[k] for k in SolveResult.__dataclass_fields__})
+
+    def solve(self, A, b, x_out, p: int, tol: float, maxit: int, x0=None, lda=None) -> SolveResult:
+        n = int(b.shape[0])
+        lda = int(A.shape[1]) if lda is None else lda
+        r = Result()
+        self._lib.ccg_solve(self._h, n, _ptr(A), lda, _ptr(b), _ptr(x0), int(p), float(tol),
+                            int(maxit), _ptr(x_out), ctypes.byref(r))
+        return self._res(r)
+
+    def solve_block(self, A, b, X0, x_out, tol: float, maxit: int, X_out=None,
+                    lda=None) -> SolveResult:
+        n = int(b.shape[0])
+        p = int(X0.shape[1])
+        lda = int(A.shape[1]) if lda is None else lda
+        r = Result()
+        self._lib.ccg_solve_block(self._h, n, _ptr(A), lda, _ptr(b), _ptr(X0), p, float(tol),
+                                  int(maxit), _ptr(x_out), _ptr(X_out), ctypes.byref(r))
+        return self._res(r)
+
+    def block_product(self, A, V, W, U=None, want_grams: bool = True, lda=None):
+        """W = A V and (M = V'W symmetrised, G = U'V) as numpy q x q arrays."""
+        n = int(V.shape[0])
+        q = int(V.shape[1])
+        lda = int(A.shape[1]) if lda is None else lda
+        M = np.zeros((q, q)) if want_grams else None
+        G = np.zeros((q, q)) if (want_grams and U is not None) else None
+        ms = ctypes.c_float(0.0)
+        rc = self._lib.ccg_block_product(self._h, n, _ptr(A), lda, _ptr(V), _ptr(U), q, _ptr(W),
+                                         _ptr(M), _ptr(G), ctypes.byref(ms))
+        return rc, M, G, ms.value
+
+    def selftest_barrier_timeout(self, timeout_ms: float) -> int:
+        return int(self._lib.ccg_selftest_barrier_timeout(self._h, float(timeout_ms)))
+
+
+def status_string(code: int) -> str:
+    return lib().ccg_status_string(int(code)).decode()
+
+
+def version() -> str:
+    return lib().ccg_version().decode()

@@ -1,0 +1,486 @@
+// ccg_capi.cu -- C ABI (include/ccg.h): argument checks, handle and workspace
+// management, host/device buffer staging, and the cooperative launch of the
+// persistent solver kernel.  No compute happens here: every arithmetic step
+// of the solve runs in the kernels of ccg_fp64.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "ccg.h"
+#include "ccg_internal.h"
+
+using ccg::DevState;
+using ccg::Params;
+
+struct ccg_handle_s {
+  ccg_config cfg;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  char* ws = nullptr;         // solver workspace
+  size_t ws_bytes = 0;
+  char* stage = nullptr;      // device copies of host inputs / outputs
+  size_t stage_bytes = 0;
+  DevState* h_state = nullptr;  // pinned host mirror of the device state
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int map_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return CCG_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return CCG_ERR_OOM;
+  }
+  return CCG_ERR_CUDA;
+}
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int ensure(char** buf, size_t* have, size_t need) {
+  if (*have >= need) return CCG_OK;
+  if (*buf) {
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+  }
+  const size_t sz = round_up(std::max<size_t>(need, 1), size_t(1) << 20);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(buf), sz);
+  if (e != cudaSuccess) {
+    *buf = nullptr;
+    return map_cuda(e);
+  }
+  *have = sz;
+  return CCG_OK;
+}
+
+// Bump allocator over a contiguous region (256-byte aligned pieces).
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(char* b) : base(b) {}
+  template <class T>
+  T* take(size_t count) {
+    off = round_up(off, 256);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+  static size_t need(std::initializer_list<size_t> bytes) {
+    size_t o = 0;
+    for (size_t b : bytes) o = round_up(o, 256) + b;
+    return round_up(o, 256);
+  }
+};
+
+int grid_size(const ccg_handle_s* h, int64_t n) {
+  int64_t g = std::min<int64_t>(h->num_sms, (n + ccg::kWarps - 1) / ccg::kWarps);
+  if (h->cfg.max_ctas > 0) g = std::min<int64_t>(g, h->cfg.max_ctas);
+  return (int)std::max<int64_t>(1, g);
+}
+
+void init_state(DevState* s, int p) {
+  std::memset(s, 0, sizeof(DevState));
+  s->pk = p;
+  s->prev_pk = p;
+  s->k_replaced = -1;
+  for (int j = 0; j < ccg::kMaxP; ++j) s->agent[j] = j;
+}
+
+// Staged view of a caller buffer: device pointer to use and, for host
+// buffers, where the device copy lives.
+struct Buf {
+  const void* user = nullptr;
+  void* dev = nullptr;
+  bool host = false;
+  size_t bytes = 0;
+};
+
+int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const double* b,
+               const double* x0, const double* X0, int p, double tol, int maxit, double* x_out,
+               double* X_out, ccg_result* res) {
+  if (res) {
+    std::memset(res, 0, sizeof(*res));
+    res->agent = -1;
+  }
+  auto fail = [&](int st) {
+    if (res) res->status = st;
+    return st;
+  };
+  if (!h || n < 1 || p < 1 || p > ccg::kMaxP || p > n || lda < n || !(tol > 0.0) ||
+      !std::isfinite(tol) || maxit < 0 || !A || !b || !x_out)
+    return fail(CCG_ERR_INVALID);
+  DeviceGuard guard(h->device);
+
+  const bool a_dev = is_device_ptr(A);
+  const bool b_dev = is_device_ptr(b);
+  const bool x0_dev = x0 ? is_device_ptr(x0) : true;
+  const bool X0_dev = X0 ? is_device_ptr(X0) : true;
+  const bool xo_dev = is_device_ptr(x_out);
+  const bool Xo_dev = X_out ? is_device_ptr(X_out) : true;
+  for (const void* ptr : {(const void*)A, (const void*)b, (const void*)x0, (const void*)X0,
+                          (const void*)x_out, (const void*)X_out})
+    if (ptr && !aligned(ptr, 8)) return fail(CCG_ERR_INVALID);
+
+  const size_t np = (size_t)n * (size_t)p;
+  // host A is staged with an even leading dimension (vectorised A stream)
+  const int64_t lda_dev = a_dev ? lda : (n + (n & 1));
+  const size_t a_bytes = a_dev ? 0 : (size_t)n * (size_t)lda_dev * sizeof(double);
+  const size_t stage_need = Carve::need({a_bytes, b_dev ? 0 : n * sizeof(double),
+                                         x0_dev ? 0 : n * sizeof(double),
+                                         X0_dev ? 0 : np * sizeof(double),
+                                         xo_dev ? 0 : n * sizeof(double),
+                                         Xo_dev ? 0 : np * sizeof(double)});
+  int rc = ensure(&h->stage, &h->stage_bytes, stage_need);
+  if (rc != CCG_OK) return fail(rc);
+
+  const int G = grid_size(h, n);
+  const size_t ws_need =
+      Carve::need({5 * np * sizeof(double), (size_t)G * ccg::kPartStride * sizeof(double),
+                   sizeof(DevState)});
+  rc = ensure(&h->ws, &h->ws_bytes, ws_need);
+  if (rc != CCG_OK) return fail(rc);
+
+  cudaStream_t s = h->stream;
+  Carve sc(h->stage);
+  const double* dA = A;
+  const double* db = b;
+  const double* dx0 = x0;
+  const double* dX0 = X0;
+  double* dxo = x_out;
+  double* dXo = X_out;
+  cudaError_t e = cudaSuccess;
+  if (!a_dev) {
+    double* t = sc.take<double>((size_t)n * lda_dev);
+    e = cudaMemcpy2DAsync(t, lda_dev * sizeof(double), A, lda * sizeof(double),
+                          n * sizeof(double), n, cudaMemcpyHostToDevice, s);
+    dA = t;
+  }
+  if (e == cudaSuccess && !b_dev) {
+    double* t = sc.take<double>(n);
+    e = cudaMemcpyAsync(t, b, n * sizeof(double), cudaMemcpyHostToDevice, s);
+    db = t;
+  }
+  if (e == cudaSuccess && !x0_dev) {
+    double* t = sc.take<double>(n);
+    e = cudaMemcpyAsync(t, x0, n * sizeof(double), cudaMemcpyHostToDevice, s);
+    dx0 = t;
+  }
+  if (e == cudaSuccess && !X0_dev) {
+    double* t = sc.take<double>(np);
+    e = cudaMemcpyAsync(t, X0, np * sizeof(double), cudaMemcpyHostToDevice, s);
+    dX0 = t;
+  }
+  if (!xo_dev) dxo = sc.take<double>(n);
+  if (!Xo_dev) dXo = sc.take<double>(np);
+  if (e != cudaSuccess) return fail(map_cuda(e));
+
+  Carve wc(h->ws);
+  Params prm{};
+  prm.n = n;
+  prm.lda = a_dev ? lda : lda_dev;
+  prm.A = dA;
+  prm.b = db;
+  prm.x0 = X0 ? nullptr : dx0;
+  prm.X0 = X0 ? dX0 : nullptr;
+  prm.spread = h->cfg.x0_spread;
+  prm.seed = h->cfg.seed;
+  prm.X = wc.take<double>(np);
+  prm.R = wc.take<double>(np);
+  prm.D0 = wc.take<double>(np);
+  prm.D1 = wc.take<double>(np);
+  prm.W = wc.take<double>(np);
+  prm.part = wc.take<double>((size_t)G * ccg::kPartStride);
+  prm.st = wc.take<DevState>(1);
+  prm.x_out = dxo;
+  prm.X_out = dXo;
+  prm.p = p;
+  prm.maxit = maxit;
+  prm.tol = tol;
+  prm.rank_tol = h->cfg.rank_tol;
+  prm.replacement = h->cfg.residual_replacement ? 1 : 0;
+  prm.mode = ccg::MODE_SOLVE;
+  prm.timeout_ns = (long long)(h->cfg.barrier_timeout_ms * 1e6);
+  prm.expected_ctas = (unsigned)G;
+
+  const int P = ccg::p_bucket(p);
+  const bool vec = (prm.lda % 2 == 0) && aligned(dA, 16);
+  if (ccg::fp64_ctas_per_sm(P, vec) < 1) return fail(CCG_ERR_CUDA);
+
+  init_state(h->h_state, p);
+  e = cudaMemcpyAsync(prm.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev0, s);
+  if (e == cudaSuccess) e = ccg::launch_fp64(prm, P, vec, G, s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev1, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_state, prm.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && !xo_dev)
+    e = cudaMemcpyAsync(x_out, dxo, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && X_out && !Xo_dev)
+    e = cudaMemcpyAsync(X_out, dXo, np * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(map_cuda(e));
+
+  const DevState& st = *h->h_state;
+  int status = st.error != 0 ? st.error : st.result;
+  if (res) {
+    res->status = status;
+    res->iterations = st.k;
+    res->agent = (st.error == 0) ? st.agent[st.jbest] : -1;
+    res->p_final = st.pk;
+    res->replacements = st.replacements;
+    res->drops = st.drops;
+    res->relres_true = st.relres_true;
+    res->relres_recur = st.relres_recur;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    res->device_ms = ms;
+    res->ctas = G;
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ccg_config_init(ccg_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->stream = nullptr;
+  cfg->precision = CCG_FP64;
+  cfg->rank_tol = 1e-12;
+  cfg->x0_spread = 1.0;
+  cfg->seed = 0;
+  cfg->residual_replacement = 1;
+  cfg->barrier_timeout_ms = 10000.0;
+  cfg->max_ctas = 0;
+}
+
+int ccg_create(ccg_handle** out, const ccg_config* cfg) {
+  if (!out) return CCG_ERR_INVALID;
+  *out = nullptr;
+  ccg_config c;
+  if (cfg) c = *cfg;
+  else ccg_config_init(&c);
+  if (!(c.rank_tol > 0.0) || !(c.barrier_timeout_ms > 0.0) || c.precision != CCG_FP64 ||
+      c.max_ctas < 0)
+    return CCG_ERR_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return CCG_ERR_CUDA;
+  }
+  if (c.device < 0 || c.device >= ndev) return CCG_ERR_INVALID;
+  ccg_handle_s* h = new (std::nothrow) ccg_handle_s();
+  if (!h) return CCG_ERR_OOM;
+  h->cfg = c;
+  h->device = c.device;
+  h->stream = static_cast<cudaStream_t>(c.stream);
+  DeviceGuard guard(h->device);
+  cudaError_t e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->h_state), sizeof(DevState));
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+  if (e != cudaSuccess) {
+    ccg_destroy(h);
+    return map_cuda(e);
+  }
+  *out = h;
+  return CCG_OK;
+}
+
+int ccg_destroy(ccg_handle* h) {
+  if (!h) return CCG_OK;
+  {
+    DeviceGuard guard(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->ws) cudaFree(h->ws);
+    if (h->stage) cudaFree(h->stage);
+    if (h->h_state) cudaFreeHost(h->h_state);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+  }
+  delete h;
+  return CCG_OK;
+}
+
+int ccg_solve(ccg_handle* h, int64_t n, const double* A, int64_t lda, const double* b,
+              const double* x0, int p, double tol, int maxit, double* x_out, ccg_result* res) {
+  return solve_impl(h, n, A, lda, b, x0, nullptr, p, tol, maxit, x_out, nullptr, res);
+}
+
+int ccg_solve_block(ccg_handle* h, int64_t n, const double* A, int64_t lda, const double* b,
+                    const double* X0, int p, double tol, int maxit, double* x_out,
+                    double* X_out, ccg_result* res) {
+  if (!X0) {
+    if (res) {
+      std::memset(res, 0, sizeof(*res));
+      res->status = CCG_ERR_INVALID;
+    }
+    return CCG_ERR_INVALID;
+  }
+  return solve_impl(h, n, A, lda, b, nullptr, X0, p, tol, maxit, x_out, X_out, res);
+}
+
+int ccg_block_product(ccg_handle* h, int64_t n, const double* A, int64_t lda, const double* V,
+                      const double* U, int q, double* W, double* M, double* G_out,
+                      float* device_ms) {
+  if (!h || n < 1 || q < 1 || q > ccg::kMaxP || lda < n || !A || !V || !W)
+    return CCG_ERR_INVALID;
+  for (const void* ptr : {(const void*)A, (const void*)V, (const void*)U, (const void*)W})
+    if (ptr && !aligned(ptr, 8)) return CCG_ERR_INVALID;
+  DeviceGuard guard(h->device);
+  const bool a_dev = is_device_ptr(A), v_dev = is_device_ptr(V);
+  const bool u_dev = U ? is_device_ptr(U) : true, w_dev = is_device_ptr(W);
+  const size_t nq = (size_t)n * (size_t)q;
+  const int64_t lda_dev = a_dev ? lda : (n + (n & 1));
+  int rc = ensure(&h->stage, &h->stage_bytes,
+                  Carve::need({a_dev ? 0 : (size_t)n * lda_dev * sizeof(double),
+                               v_dev ? 0 : nq * sizeof(double), u_dev ? 0 : nq * sizeof(double),
+                               w_dev ? 0 : nq * sizeof(double)}));
+  if (rc != CCG_OK) return rc;
+  const int G = grid_size(h, n);
+  rc = ensure(&h->ws, &h->ws_bytes,
+              Carve::need({(size_t)G * ccg::kPartStride * sizeof(double), sizeof(DevState)}));
+  if (rc != CCG_OK) return rc;
+  cudaStream_t s = h->stream;
+  Carve sc(h->stage);
+  const double* dA = A;
+  const double* dV = V;
+  const double* dU = U;
+  double* dW = W;
+  cudaError_t e = cudaSuccess;
+  if (!a_dev) {
+    double* t = sc.take<double>((size_t)n * lda_dev);
+    e = cudaMemcpy2DAsync(t, lda_dev * sizeof(double), A, lda * sizeof(double),
+                          n * sizeof(double), n, cudaMemcpyHostToDevice, s);
+    dA = t;
+  }
+  if (e == cudaSuccess && !v_dev) {
+    double* t = sc.take<double>(nq);
+    e = cudaMemcpyAsync(t, V, nq * sizeof(double), cudaMemcpyHostToDevice, s);
+    dV = t;
+  }
+  if (e == cudaSuccess && U && !u_dev) {
+    double* t = sc.take<double>(nq);
+    e = cudaMemcpyAsync(t, U, nq * sizeof(double), cudaMemcpyHostToDevice, s);
+    dU = t;
+  }
+  if (!w_dev) dW = sc.take<double>(nq);
+  if (e != cudaSuccess) return map_cuda(e);
+
+  Carve wc(h->ws);
+  Params prm{};
+  prm.n = n;
+  prm.lda = a_dev ? lda : lda_dev;
+  prm.A = dA;
+  prm.part = wc.take<double>((size_t)G * ccg::kPartStride);
+  prm.st = wc.take<DevState>(1);
+  prm.mode = ccg::MODE_BLOCK_PRODUCT;
+  prm.timeout_ns = (long long)(h->cfg.barrier_timeout_ms * 1e6);
+  prm.expected_ctas = (unsigned)G;
+  prm.V = dV;
+  prm.U = dU;
+  prm.Wout = dW;
+  prm.q = q;
+  prm.p = q;
+  const int P = ccg::p_bucket(q);
+  const bool vec = (prm.lda % 2 == 0) && aligned(dA, 16);
+  if (ccg::fp64_ctas_per_sm(P, vec) < 1) return CCG_ERR_CUDA;
+  init_state(h->h_state, q);
+  e = cudaMemcpyAsync(prm.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev0, s);
+  if (e == cudaSuccess) e = ccg::launch_fp64(prm, P, vec, G, s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev1, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_state, prm.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && !w_dev)
+    e = cudaMemcpyAsync(W, dW, nq * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return map_cuda(e);
+  const DevState& st = *h->h_state;
+  if (st.error != 0) return st.error;
+  for (int a = 0; a < q; ++a)
+    for (int c = 0; c < q; ++c) {
+      if (M) M[a * q + c] = st.gram_out[a * ccg::kMaxP + c];
+      if (G_out && U) G_out[a * q + c] = st.gram_out[ccg::kSq + a * ccg::kMaxP + c];
+    }
+  if (device_ms) cudaEventElapsedTime(device_ms, h->ev0, h->ev1);
+  return CCG_OK;
+}
+
+int ccg_selftest_barrier_timeout(ccg_handle* h, double timeout_ms) {
+  if (!h || !(timeout_ms > 0.0) || timeout_ms > 60000.0) return CCG_ERR_INVALID;
+  DeviceGuard guard(h->device);
+  const int G = 2;
+  int rc = ensure(&h->ws, &h->ws_bytes,
+                  Carve::need({(size_t)G * ccg::kPartStride * sizeof(double), sizeof(DevState)}));
+  if (rc != CCG_OK) return rc;
+  Carve wc(h->ws);
+  Params prm{};
+  prm.n = 1;
+  prm.lda = 1;
+  prm.part = wc.take<double>((size_t)G * ccg::kPartStride);
+  prm.st = wc.take<DevState>(1);
+  prm.mode = ccg::MODE_BARRIER_SELFTEST;
+  prm.timeout_ns = (long long)(timeout_ms * 1e6);
+  prm.expected_ctas = (unsigned)G + 1u;  // one arrival more than the grid holds
+  cudaStream_t s = h->stream;
+  init_state(h->h_state, 1);
+  cudaError_t e = cudaMemcpyAsync(prm.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = ccg::launch_fp64(prm, 1, false, G, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_state, prm.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return map_cuda(e);
+  return h->h_state->error;
+}
+
+const char* ccg_status_string(int status) {
+  switch (status) {
+    case CCG_OK: return "CCG_OK";
+    case CCG_NOT_CONVERGED: return "CCG_NOT_CONVERGED";
+    case CCG_ERR_INVALID: return "CCG_ERR_INVALID";
+    case CCG_ERR_NOT_SPD: return "CCG_ERR_NOT_SPD";
+    case CCG_ERR_NUMERICAL: return "CCG_ERR_NUMERICAL";
+    case CCG_ERR_OOM: return "CCG_ERR_OOM";
+    case CCG_ERR_TIMEOUT: return "CCG_ERR_TIMEOUT";
+    case CCG_ERR_CUDA: return "CCG_ERR_CUDA";
+    default: return "CCG_UNKNOWN_STATUS";
+  }
+}
+
+const char* ccg_version(void) { return "ccg-gb300 0.1 (fp64 persistent)"; }
+
+}  // extern "C"

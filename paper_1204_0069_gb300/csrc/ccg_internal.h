@@ -1,0 +1,123 @@
+// ccg_internal.h -- state and launch parameters shared by the C-ABI layer and
+// the persistent FP64 solver kernel.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ccg {
+
+constexpr int kMaxP = 32;          // agents per solve (warp width)
+constexpr int kThreads = 256;      // threads per CTA of the persistent kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kSq = kMaxP * kMaxP;
+// Per-CTA partial-sum slot: two p x p Grams, one p-vector, one scalar.
+constexpr int kSlotGram0 = 0;
+constexpr int kSlotGram1 = kSq;
+constexpr int kSlotVec = 2 * kSq;
+constexpr int kSlotScalar = 2 * kSq + kMaxP;
+constexpr int kPartStride = 2 * kSq + 2 * kMaxP;
+
+// Control word written by the CTA that runs a serial step; every CTA follows
+// it after the grid barrier, so control flow is uniform across the grid.
+enum Ctrl : int {
+  CTRL_LOOP = 0,     // run one cCG iteration
+  CTRL_CHECK = 1,    // true residual of the best agent
+  CTRL_REPLACE = 2,  // residual replacement R = A X - b 1^T, D = R
+  CTRL_FINISH = 3    // write x_out / X_out and leave
+};
+
+enum Mode : int {
+  MODE_SOLVE = 0,
+  MODE_BLOCK_PRODUCT = 1,
+  MODE_BARRIER_SELFTEST = 2
+};
+
+// Status values mirror ccg_status in include/ccg.h.
+enum Status : int {
+  ST_OK = 0,
+  ST_NOT_CONVERGED = 1,
+  ST_ERR_INVALID = -1,
+  ST_ERR_NOT_SPD = -2,
+  ST_ERR_NUMERICAL = -3,
+  ST_ERR_OOM = -4,
+  ST_ERR_TIMEOUT = -5,
+  ST_ERR_CUDA = -6
+};
+
+// Device-resident solver state (one per launch, in the handle workspace).
+struct DevState {
+  unsigned int bar_count;   // grid barrier arrivals
+  unsigned int bar_gen;     // grid barrier generation
+  int error;                // first error (negative status), 0 if none
+  int result;               // ST_OK / ST_NOT_CONVERGED once finished
+  int ctrl;                 // Ctrl for the next phase
+  int k;                    // iterations so far
+  int pk;                   // active agents
+  int prev_pk;              // active agents before the last rank test
+  int changed;              // 1 if the last rank test removed agents
+  int jbest;                // column of the agent returned
+  int replacements;
+  int drops;
+  int k_replaced;           // iteration count at the last replacement
+  int zero_rhs;             // b == 0
+  int err_where;            // diagnostic: phase that set `error`
+  int pad0;
+  int keep[kMaxP];          // kept columns (pre-compaction indices)
+  int agent[kMaxP];         // original agent id of each active column
+  int old_agent[kMaxP];     // agent ids before the last compaction
+  double bnorm;
+  double relres_true;
+  double relres_recur;
+  double s[kMaxP];          // ||R e_j||
+  double sc[kMaxP];         // diag(M)^{-1/2} of the kept columns
+  double L[kSq];            // Cholesky factor of S M S (stride kMaxP)
+  double alphaT[kSq];       // (alpha_k^T)[b][a], stride kMaxP
+  double betaT[kSq];        // (beta_k^T)[b][a], stride kMaxP
+  double gram_out[2 * kSq]; // block-product mode: M, G (stride kMaxP)
+};
+
+struct Params {
+  int64_t n;
+  int64_t lda;
+  const double* A;
+  const double* b;
+  const double* x0;        // ccg_solve: single initial guess (nullable)
+  const double* X0;        // ccg_solve_block: explicit initial block
+  double spread;
+  unsigned long long seed;
+  double* X;
+  double* R;
+  double* D0;
+  double* D1;
+  double* W;
+  double* part;            // gridDim.x * kPartStride partial sums
+  DevState* st;
+  double* x_out;
+  double* X_out;           // nullable, n x p
+  int p;                   // agents requested (leading dimension of blocks)
+  int maxit;
+  double tol;
+  double rank_tol;
+  int replacement;
+  int mode;
+  long long timeout_ns;
+  unsigned int expected_ctas;  // barrier arrival count
+  // block-product mode
+  const double* V;
+  const double* U;
+  double* Wout;
+  int q;
+};
+
+// Launch helpers implemented in ccg_fp64.cu.
+// Bucket (1, 2, 4, 8, 16, 32) >= p used for the register tiles.
+int p_bucket(int p);
+// Dynamic shared memory the kernel needs for bucket P.
+size_t fp64_smem_bytes(int P);
+// Max co-resident CTAs per SM of the FP64 kernel (0 on error).
+int fp64_ctas_per_sm(int P, bool vec);
+cudaError_t launch_fp64(const Params& prm, int P, bool vec, int ctas,
+                        cudaStream_t stream);
+
+}  // namespace ccg
