@@ -43,6 +43,16 @@
  *   - The stop test is min_j ||R e_j|| <= tol ||b||; the returned agent is
  *     the argmin (lowest index on ties).
  *   - Iterations = number of alpha computations (A D products in the loop).
+ *   - The p x p Gram products D'AD, R'D, R'AD (Table 1, rows 2, 3 and 7),
+ *     the residue norms ||R e_j|| and ||b|| are inner products that the
+ *     method's analysis takes as exact (Sec. 4 works in exact arithmetic);
+ *     they decide the matrix stepsizes and the stop test, and the iteration
+ *     count of an ill-conditioned solve is sensitive to their rounding.  They
+ *     are evaluated with the compensated dot product Dot2 of Ogita, Rump and
+ *     Oishi (SIAM J. Sci. Comput. 26, 2005), which is as accurate as a dot
+ *     product computed in twice the working precision and then rounded, so
+ *     their value does not depend on n or on the order of summation.  The
+ *     block product W = A D is a plain sequential sum.
  *
  * Storage: every n x p block is row-major with leading dimension p
  * (element (i, j) at [i*p + j]); A is row-major with leading dimension lda.
@@ -135,14 +145,57 @@ static void mat_block(int64_t n, const double* A, int64_t lda, const double* V,
     }
 }
 
-/* G = U^T V (q x q), G[a][b] = sum_i U[i][a] V[i][b], sequential in i. */
+/* Error-free transformations, exact in binary64 without FMA contraction:
+ * Knuth's TwoSum and Dekker's TwoProduct with Veltkamp's splitting. */
+static void two_sum(double a, double b, double* s, double* e)
+{
+    double x = a + b;
+    double z = x - a;
+    *e = (a - (x - z)) + (b - z);
+    *s = x;
+}
+
+static void split27(double a, double* hi, double* lo)
+{
+    double c = 134217729.0 * a; /* 2^27 + 1 */
+    double h = c - (c - a);
+    *hi = h;
+    *lo = a - h;
+}
+
+static void two_prod(double a, double b, double* p, double* e)
+{
+    double x = a * b, ah, al, bh, bl;
+    split27(a, &ah, &al);
+    split27(b, &bh, &bl);
+    *e = al * bl - (((x - ah * bh) - al * bh) - ah * bl);
+    *p = x;
+}
+
+/* Dot2 accumulator: running sum s and the accumulated rounding errors c. */
+typedef struct { double s, c; } dot2_t;
+
+static void dot2_add(dot2_t* t, double x, double y)
+{
+    double p, e, s, f;
+    two_prod(x, y, &p, &e);
+    two_sum(t->s, p, &s, &f);
+    t->s = s;
+    t->c += e + f;
+}
+
+static double dot2_value(dot2_t t) { return t.s + t.c; }
+
+/* G = U^T V (q x q), G[a][b] = sum_i U[i][a] V[i][b] (Dot2, i = 0..n-1). */
 static void gram(int64_t n, int q, const double* U, const double* V, double* G)
 {
-    for (int e = 0; e < q * q; ++e) G[e] = 0.0;
+    dot2_t acc[32 * 32];
+    for (int e = 0; e < q * q; ++e) { acc[e].s = 0.0; acc[e].c = 0.0; }
     for (int64_t i = 0; i < n; ++i)
         for (int a = 0; a < q; ++a)
             for (int c = 0; c < q; ++c)
-                G[a * q + c] += U[i * q + a] * V[i * q + c];
+                dot2_add(&acc[a * q + c], U[i * q + a], V[i * q + c]);
+    for (int e = 0; e < q * q; ++e) G[e] = dot2_value(acc[e]);
 }
 
 /* Y += Z T  with Z n x q and T q x q row-major. */
@@ -157,13 +210,14 @@ static void add_block_times(int64_t n, int q, double* Y, const double* Z,
         }
 }
 
-/* Column norms s_j = ||R e_j||. */
+/* Column norms s_j = ||R e_j|| (Dot2). */
 static void col_norms(int64_t n, int q, const double* R, double* s)
 {
-    for (int j = 0; j < q; ++j) s[j] = 0.0;
+    dot2_t acc[32];
+    for (int j = 0; j < q; ++j) { acc[j].s = 0.0; acc[j].c = 0.0; }
     for (int64_t i = 0; i < n; ++i)
-        for (int j = 0; j < q; ++j) s[j] += R[i * q + j] * R[i * q + j];
-    for (int j = 0; j < q; ++j) s[j] = sqrt(s[j]);
+        for (int j = 0; j < q; ++j) dot2_add(&acc[j], R[i * q + j], R[i * q + j]);
+    for (int j = 0; j < q; ++j) s[j] = sqrt(dot2_value(acc[j]));
 }
 
 /* Keep columns listed in keep[0..m) of an n x q block, in place -> n x m. */
@@ -275,18 +329,18 @@ static double true_relres(int64_t n, const double* A, int64_t lda,
         for (int64_t l = 0; l < n; ++l) ax += Ai[l] * X[l * q + j];
         r[i] = b[i] - ax;
     }
-    double acc = 0.0;
-    for (int64_t i = 0; i < n; ++i) acc += r[i] * r[i];
+    dot2_t acc = {0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i) dot2_add(&acc, r[i], r[i]);
     free(r);
-    return sqrt(acc) / bnorm;
+    return sqrt(dot2_value(acc)) / bnorm;
 }
 
 double oracle_true_relres(int64_t n, const double* A, int64_t lda,
                           const double* b, const double* x, int nthreads)
 {
-    double bn = 0.0;
-    for (int64_t i = 0; i < n; ++i) bn += b[i] * b[i];
-    bn = sqrt(bn);
+    dot2_t bacc = {0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i) dot2_add(&bacc, b[i], b[i]);
+    double bn = sqrt(dot2_value(bacc));
     if (bn == 0.0) bn = 1.0;
     return true_relres(n, A, lda, b, x, 1, 0, bn, nthreads < 1 ? 1 : nthreads);
 }
@@ -328,9 +382,9 @@ int oracle_ccg(int64_t n, const double* A, int64_t lda, const double* b,
     int pk = p, k = 0, status = ORC_NOT_CONVERGED;
     int k_replaced = -1; /* iteration count at the last replacement */
 
-    double bnorm = 0.0;
-    for (int64_t i = 0; i < n; ++i) bnorm += b[i] * b[i];
-    bnorm = sqrt(bnorm);
+    dot2_t bacc = {0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i) dot2_add(&bacc, b[i], b[i]);
+    double bnorm = sqrt(dot2_value(bacc));
     for (int j = 0; j < p; ++j) agent[j] = j;
 
     if (bnorm == 0.0) { /* x* = 0 */

@@ -11,12 +11,15 @@ constexpr int kMaxP = 32;          // agents per solve (warp width)
 constexpr int kThreads = 256;      // threads per CTA of the persistent kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kSq = kMaxP * kMaxP;
-// Per-CTA partial-sum slot: two p x p Grams, one p-vector, one scalar.
+// Per-CTA partial-sum slot: two p x p Grams, one p-vector, one scalar, each
+// entry as an unevaluated sum hi + lo (compensated accumulation): hi at
+// [slot], lo at [kPartHalf + slot].
 constexpr int kSlotGram0 = 0;
 constexpr int kSlotGram1 = kSq;
 constexpr int kSlotVec = 2 * kSq;
 constexpr int kSlotScalar = 2 * kSq + kMaxP;
-constexpr int kPartStride = 2 * kSq + 2 * kMaxP;
+constexpr int kPartHalf = 2 * kSq + 2 * kMaxP;
+constexpr int kPartStride = 2 * kPartHalf;
 
 // Control word written by the CTA that runs a serial step; every CTA follows
 // it after the grid barrier, so control flow is uniform across the grid.

@@ -101,13 +101,15 @@ def test_direct_solve(oracle_mod, n, p, cond):
 def test_relative_stop_test_is_scale_invariant(oracle_mod):
     """Stop rule min_j ||R e_j|| <= tol ||b|| (Algorithm 4, read as relative):
     scaling b and X_0 together scales every residue and leaves the iteration
-    count unchanged; an absolute test would not."""
+    count unchanged; an absolute test would not.  A power-of-two scale makes
+    every rounding scale with it, so the result scales bitwise."""
     A, b = wl.random_spd(40, seed=3, cond=50.0)
     X0 = wl.random_block(40, 3, seed=4)
+    s = 2.0 ** 20
     r1 = oracle_mod.ccg(A, b, X0, tol=1e-9, maxit=400)
-    r2 = oracle_mod.ccg(A, 1e6 * b, 1e6 * X0, tol=1e-9, maxit=400)
+    r2 = oracle_mod.ccg(A, s * b, s * X0, tol=1e-9, maxit=400)
     assert r1["iterations"] == r2["iterations"]
-    np.testing.assert_allclose(r2["x"], 1e6 * r1["x"], rtol=1e-9, atol=0)
+    assert np.array_equal(r2["x"], s * r1["x"])
 
 
 # --------------------------------------------------------------------------
@@ -404,3 +406,12 @@ def test_nan_input_detected(oracle_mod):
     A, b = wl.random_spd(10, seed=9)
     b[3] = np.nan
     assert oracle_mod.ccg(A, b, wl.random_block(10, 2, seed=1), 1e-8, 10)["status"] == -3
+
+
+def test_true_relres_helper_matches_numpy(oracle_mod):
+    """The oracle's exit check ||b - A x|| / ||b|| (Algorithm 4's stop test
+    verified on the true residual) against numpy's norm of b - A @ x."""
+    A, b = wl.random_spd(37, seed=17, cond=30.0)
+    x = wl.random_block(37, 1, seed=18)[:, 0]
+    ref = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    assert abs(oracle_mod.true_relres(A, b, x) - ref) <= 1e-14 * ref
