@@ -17,8 +17,13 @@
 //   D-update D_{k+1} = R_{k+1} + D_k beta^T                  (Table 1, row 9)
 //   barrier
 //
-// All cross-CTA sums run in a fixed order (CTA 0, 1, ...), so a solve is
-// bitwise reproducible for a fixed grid.  Every wait on another CTA gives up
+// The p x p Grams and the norms are inner products that the method treats as
+// exact (Sec. 4 works in exact arithmetic); they decide the matrix stepsizes
+// and the stop test, so they are accumulated with error-free transformations
+// (Dot2 of Ogita, Rump and Oishi 2005: exact products by FMA, TwoSum for the
+// running sum) per CTA and again across CTAs.  All cross-CTA sums run in a
+// fixed order (CTA 0, 1, ...), so a solve is bitwise reproducible for a fixed
+// grid.  Every wait on another CTA gives up
 // after Params::timeout_ns and sets CCG_ERR_TIMEOUT; all CTAs then return.
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -56,6 +61,47 @@ __device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
 
 __device__ void set_error(DevState* st, int code, int where) {
   if (atomicCAS(&st->error, 0, code) == 0) st->err_where = where;
+}
+
+// Compensated accumulation (Dot2).  The intrinsics keep the compiler from
+// contracting the error-free transformations into FMAs.
+struct DSum {
+  double hi;
+  double lo;
+};
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  const double z = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, z)), __dsub_rn(b, z));
+}
+__device__ __forceinline__ void dsum_fma(DSum& t, double x, double y) {
+  const double p = __dmul_rn(x, y);
+  const double pe = fma(x, y, -p);  // exact product error
+  double s, e;
+  two_sum(t.hi, p, s, e);
+  t.hi = s;
+  t.lo = __dadd_rn(t.lo, __dadd_rn(pe, e));
+}
+__device__ __forceinline__ void dsum_add(DSum& t, double hi, double lo) {
+  double s, e;
+  two_sum(t.hi, hi, s, e);
+  t.hi = s;
+  t.lo = __dadd_rn(t.lo, __dadd_rn(lo, e));
+}
+// Warp-wide compensated sum in a fixed butterfly order; all lanes get it.
+__device__ __forceinline__ DSum dsum_warp(DSum t) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const double oh = __shfl_xor_sync(0xffffffffu, t.hi, m);
+    const double ol = __shfl_xor_sync(0xffffffffu, t.lo, m);
+    // combine in lane order so both partners compute the same value
+    const bool low = (threadIdx.x & m) == 0;
+    DSum a = low ? t : DSum{oh, ol};
+    const DSum b = low ? DSum{oh, ol} : t;
+    dsum_add(a, b.hi, b.lo);
+    t = a;
+  }
+  return t;
 }
 
 // --------------------------------------------------------------------------
@@ -131,16 +177,23 @@ __device__ bool grid_barrier(const Params& prm, SyncShared* ss, int* s_err) {
 // --------------------------------------------------------------------------
 // Block product tile shapes.  Lanes of a warp split the k range of one row
 // of A (two consecutive k per lane, 16-byte loads); a k-chunk of the operand
-// V is staged transposed in shared memory and reused by the CTA's 8 rows of
-// the pass.  NS independent accumulator sets keep >= 8 FMA chains per lane.
+// V (BK x P) is staged transposed in shared memory and shared by the CTA's 8
+// rows of the pass.  The next chunk's A values (registers) and V values
+// (registers, then the second shared buffer) are fetched while the current
+// chunk is multiplied, so each chunk costs one CTA barrier and the memory
+// latency hides behind the FP64 pipe.  NS independent accumulator sets keep
+// >= 8 FMA chains per lane.
 // --------------------------------------------------------------------------
 template <int P>
 struct Tile {
-  static constexpr int BK = (P >= 8) ? 128 : 1024 / P;
-  static constexpr int VSTR = BK + 2;
+  static constexpr int BK = (2048 / P < 512) ? 2048 / P : 512;
+  static constexpr int VSTR = BK + 2;          // padded shared row (16-byte aligned)
   static constexpr int NS = (P >= 8) ? 1 : 8 / P;
+  static constexpr int NLD = BK / 64;          // double2 loads of A per lane per chunk
+  static constexpr int NV = BK * P / kThreads; // staged V values per thread per chunk
   static constexpr int LOGP = (P == 1) ? 0 : (P == 2) ? 1 : (P == 4) ? 2
                              : (P == 8) ? 3 : (P == 16) ? 4 : 5;
+  static_assert(NV >= 1 && NV * kThreads == BK * P, "chunk must tile the CTA");
 };
 
 // Reduce-scatter over the 32 lanes: afterwards v[0] holds, in every lane, the
@@ -165,8 +218,49 @@ struct ReduceScatter {
   }
 };
 
+template <int P>
+__device__ __forceinline__ void load_v_chunk(const double* __restrict__ V, int ldv, int coff,
+                                             int pk, int64_t n, int64_t k0, double (&v)[Tile<P>::NV]) {
+#pragma unroll
+  for (int t = 0; t < Tile<P>::NV; ++t) {
+    const int idx = threadIdx.x + t * kThreads;
+    const int kk = idx >> Tile<P>::LOGP;
+    const int c = idx & (P - 1);
+    const int64_t k = k0 + kk;
+    v[t] = (c < pk && k < n) ? ldcg(V + k * ldv + coff + c) : 0.0;
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void store_v_chunk(double* Vb, const double (&v)[Tile<P>::NV]) {
+#pragma unroll
+  for (int t = 0; t < Tile<P>::NV; ++t) {
+    const int idx = threadIdx.x + t * kThreads;
+    Vb[(idx & (P - 1)) * Tile<P>::VSTR + (idx >> Tile<P>::LOGP)] = v[t];
+  }
+}
+
+template <int P, bool VEC>
+__device__ __forceinline__ void load_a_chunk(const double* Arow, int64_t n, int64_t k0, int lane,
+                                             bool valid, double2 (&a)[Tile<P>::NLD]) {
+#pragma unroll
+  for (int j = 0; j < Tile<P>::NLD; ++j) {
+    const int64_t k = k0 + j * 64 + 2 * lane;
+    double2 v = make_double2(0.0, 0.0);
+    if (valid) {
+      if (VEC && k + 1 < n) {
+        v = __ldcs(reinterpret_cast<const double2*>(Arow + k));
+      } else {
+        if (k < n) v.x = __ldcs(Arow + k);
+        if (k + 1 < n) v.y = __ldcs(Arow + k + 1);
+      }
+    }
+    a[j] = v;
+  }
+}
+
 // Y[row, c] = sum_k A[row, k] V[k, coff + c] (- b[row]) for the rows
-// [r0, r1) and c < pk.  Vs: shared scratch of P * VSTR doubles.
+// [r0, r1) and c < pk.  Vs: shared scratch of 2 * P * VSTR doubles.
 template <int P, bool VEC>
 __device__ void apass(const Params& prm, const double* __restrict__ V, int ldv,
                       int coff, int pk, double* __restrict__ Y, int ldy,
@@ -180,6 +274,7 @@ __device__ void apass(const Params& prm, const double* __restrict__ V, int ldv,
   const int64_t w0 = r0 + (nr * warp) / kWarps;
   const int64_t w1 = r0 + (nr * (warp + 1)) / kWarps;
   const int64_t passes = (nr + kWarps - 1) / kWarps;
+  const int64_t nch = (n + T::BK - 1) / T::BK;
   const double* __restrict__ A = prm.A;
 
   for (int64_t ps = 0; ps < passes; ++ps) {
@@ -192,44 +287,35 @@ __device__ void apass(const Params& prm, const double* __restrict__ V, int ldv,
 #pragma unroll
       for (int c = 0; c < P; ++c) acc[s][c] = 0.0;
 
-    for (int64_t k0 = 0; k0 < n; k0 += T::BK) {
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < T::BK * P; idx += kThreads) {
-        const int kk = idx >> T::LOGP;
-        const int c = idx & (P - 1);
-        const int64_t k = k0 + kk;
-        double v = 0.0;
-        if (c < pk && k < n) v = ldcg(V + k * ldv + coff + c);
-        Vs[c * T::VSTR + kk] = v;
+    double vreg[T::NV];
+    double2 acur[T::NLD], anxt[T::NLD];
+    load_v_chunk<P>(V, ldv, coff, pk, n, 0, vreg);
+    load_a_chunk<P, VEC>(Arow, n, 0, lane, valid, acur);
+    store_v_chunk<P>(Vs, vreg);
+    __syncthreads();
+    for (int64_t ch = 0; ch < nch; ++ch) {
+      const bool more = ch + 1 < nch;
+      if (more) {
+        load_v_chunk<P>(V, ldv, coff, pk, n, (ch + 1) * T::BK, vreg);
+        load_a_chunk<P, VEC>(Arow, n, (ch + 1) * T::BK, lane, valid, anxt);
       }
-      __syncthreads();
+      const double* Vb = Vs + (ch & 1) * (P * T::VSTR);
       if (valid) {
 #pragma unroll
-        for (int j = 0; j < T::BK / 64; ++j) {
+        for (int j = 0; j < T::NLD; ++j) {
           const int kk = j * 64 + 2 * lane;
-          const int64_t k = k0 + kk;
-          double ax, ay;
-          if (VEC) {
-            if (k + 1 < n) {
-              const double2 a2 = __ldcs(reinterpret_cast<const double2*>(Arow + k));
-              ax = a2.x;
-              ay = a2.y;
-            } else {
-              ax = (k < n) ? __ldcs(Arow + k) : 0.0;
-              ay = 0.0;
-            }
-          } else {
-            ax = (k < n) ? __ldcs(Arow + k) : 0.0;
-            ay = (k + 1 < n) ? __ldcs(Arow + k + 1) : 0.0;
-          }
 #pragma unroll
           for (int c = 0; c < P; ++c) {
-            const double2 v = *reinterpret_cast<const double2*>(Vs + c * T::VSTR + kk);
-            acc[(2 * j) % T::NS][c] = fma(ax, v.x, acc[(2 * j) % T::NS][c]);
-            acc[(2 * j + 1) % T::NS][c] = fma(ay, v.y, acc[(2 * j + 1) % T::NS][c]);
+            const double2 v = *reinterpret_cast<const double2*>(Vb + c * T::VSTR + kk);
+            acc[(2 * j) % T::NS][c] = fma(acur[j].x, v.x, acc[(2 * j) % T::NS][c]);
+            acc[(2 * j + 1) % T::NS][c] = fma(acur[j].y, v.y, acc[(2 * j + 1) % T::NS][c]);
           }
         }
       }
+      if (more) store_v_chunk<P>(Vs + ((ch + 1) & 1) * (P * T::VSTR), vreg);
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < T::NLD; ++j) acur[j] = anxt[j];
     }
     double tot[P];
 #pragma unroll
@@ -255,7 +341,8 @@ __device__ void apass(const Params& prm, const double* __restrict__ V, int ldv,
 // dimension ld:  out[g0 + a*kMaxP + c] = sum_i U0[i,a] V0[i,c]  (U0 != NULL)
 //                out[g1 + a*kMaxP + c] = sum_i U1[i,a] V1[i,c]  (U1 != NULL)
 //                out[kSlotVec + a]    = sum_i S[i,a]^2          (S != NULL)
-// Each entry is one thread's sequential sum over i (deterministic).
+// Each entry is one thread's compensated sum over i in row order (hi at
+// [slot], lo at [kPartHalf + slot]).
 __device__ void partial_grams(const double* U0, const double* V0, const double* U1,
                               const double* V1, const double* S, int ld, int pk,
                               int64_t r0, int64_t r1, double* out) {
@@ -274,9 +361,27 @@ __device__ void partial_grams(const double* U0, const double* V0, const double* 
       U = S; Vv = S; a = c = e - 2 * sq; slot = kSlotVec + a;
     }
     if (U == nullptr) continue;
-    double s = 0.0;
-    for (int64_t i = r0; i < r1; ++i) s = fma(ldcg(U + i * ld + a), ldcg(Vv + i * ld + c), s);
-    out[slot] = s;
+    DSum t{0.0, 0.0};
+    for (int64_t i = r0; i < r1; ++i) dsum_fma(t, ldcg(U + i * ld + a), ldcg(Vv + i * ld + c));
+    out[slot] = t.hi;
+    out[kPartHalf + slot] = t.lo;
+  }
+}
+
+// Per-CTA compensated sum of squares of x[i * ld] over the rows [r0, r1)
+// by warp 0, into the scalar slot.
+__device__ void partial_sumsq(const double* x, int ld, int64_t r0, int64_t r1, double* out) {
+  if (threadIdx.x < 32) {
+    DSum t{0.0, 0.0};
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += 32) {
+      const double v = ldcg(x + i * ld);
+      dsum_fma(t, v, v);
+    }
+    t = dsum_warp(t);
+    if (threadIdx.x == 0) {
+      out[kSlotScalar] = t.hi;
+      out[kPartHalf + kSlotScalar] = t.lo;
+    }
   }
 }
 
@@ -295,12 +400,15 @@ struct SerialSmem {
   int flag[4];
 };
 
-// Sum slot entries over the CTAs in fixed order.
+// Compensated sum of a slot entry over the CTAs, in CTA order.
 __device__ __forceinline__ double sum_parts(const Params& prm, int off) {
-  double s = 0.0;
+  DSum t{0.0, 0.0};
   const int G = gridDim.x;
-  for (int g = 0; g < G; ++g) s += ldcg(prm.part + (size_t)g * kPartStride + off);
-  return s;
+  for (int g = 0; g < G; ++g) {
+    const double* q = prm.part + (size_t)g * kPartStride;
+    dsum_add(t, ldcg(q + off), ldcg(q + kPartHalf + off));
+  }
+  return __dadd_rn(t.hi, t.lo);
 }
 
 // Y <- L^{-T} L^{-1} Y for m right-hand sides (thread per column), L lower.
@@ -683,13 +791,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_kernel(const __grid_constant
     }
     prm.X[idx] = v;
   }
-  if (tid < 32) {
-    double s = 0.0;
-    for (int64_t i = r0 + tid; i < r1; i += 32) s = fma(prm.b[i], prm.b[i], s);
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    if (tid == 0) mypart[kSlotScalar] = s;
-  }
+  partial_sumsq(prm.b, 1, r0, r1, mypart);
   CCG_SYNC_SERIAL(serial_bnorm(prm, S));
 
   if (tid == 0) s_int[0] = ldcg(&st->ctrl);
@@ -734,16 +836,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_kernel(const __grid_constant
       // true residual of the best agent: W[:, 0] = A X e_jb - b
       const int jb = ldcg(&st->jbest);
       apass<1, VEC>(prm, prm.X, p, jb, 1, prm.W, p, true, r0, r1, smem);
-      if (tid < 32) {
-        double s = 0.0;
-        for (int64_t i = r0 + tid; i < r1; i += 32) {
-          const double r = ldcg(prm.W + i * p);
-          s = fma(r, r, s);
-        }
-#pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-        if (tid == 0) mypart[kSlotScalar] = s;
-      }
+      partial_sumsq(prm.W, p, r0, r1, mypart);
       CCG_SYNC_SERIAL(serial_check(prm));
       continue;
     }
@@ -867,7 +960,7 @@ void* select_kernel(int P, bool vec) {
 
 template <int P>
 constexpr size_t vs_bytes() {
-  return sizeof(double) * (size_t)P * Tile<P>::VSTR;
+  return 2 * sizeof(double) * (size_t)P * Tile<P>::VSTR;
 }
 
 }  // namespace
