@@ -154,6 +154,44 @@ int ccg_block_product(ccg_handle* handle, int64_t n, const double* A, int64_t ld
  */
 int ccg_selftest_barrier_timeout(ccg_handle* handle, double timeout_ms);
 
+/* ---- Mixed precision: a quantised copy of A on the tensor cores ---------- */
+
+/* Storage formats of a quantised copy of A. */
+typedef enum {
+    CCG_LOWP_BF16 = 0,      /* bfloat16, round to nearest (2 bytes/entry)      */
+    CCG_LOWP_FP8_E4M3 = 1   /* FP8 E4M3, one FP32 scale per row: A_ij ~= s_i q_ij,
+                               s_i = max_j |A_ij| / 448 (1 byte/entry)        */
+} ccg_lowp_format;
+
+/* Opaque quantised matrix (device memory owned by the object). */
+typedef struct ccg_lowp_matrix_s ccg_lowp_matrix;
+
+/*
+ * Quantise A (n x n, lda; device or host FP64) into `format` on the handle's
+ * device and stream.  Rows are padded to a multiple of 128 entries.  The
+ * object keeps no reference to A.  Errors: CCG_ERR_INVALID (bad format, n < 1,
+ * lda < n, NULL), CCG_ERR_OOM, CCG_ERR_CUDA.
+ */
+int ccg_lowp_create(ccg_handle* handle, int format, int64_t n, const double* A, int64_t lda,
+                    ccg_lowp_matrix** out);
+
+/*
+ * Low-precision block product of Table 1, row 1: W = A_lp V for V n x q
+ * (row-major FP64, 1 <= q <= 32), W n x q row-major FP64.  V is rounded to
+ * BF16 (BF16 A) or split into two FP8 E4M3 terms with one scale per column
+ * (FP8 A); products accumulate in FP32 on the tensor cores.  device_ms
+ * (optional) receives the device time of the block product kernels.
+ * Returns CCG_ERR_TIMEOUT if an in-kernel wait gave up.
+ */
+int ccg_lowp_block_product(ccg_handle* handle, const ccg_lowp_matrix* m, const double* V, int q,
+                           double* W, float* device_ms);
+
+/* Bytes of device memory held by the quantised matrix (entries + scales). */
+int64_t ccg_lowp_bytes(const ccg_lowp_matrix* m);
+
+/* Free the quantised matrix.  NULL-safe. */
+int ccg_lowp_destroy(ccg_lowp_matrix* m);
+
 /* Name of a status code ("CCG_OK", ...). */
 const char* ccg_status_string(int status);
 

@@ -21,7 +21,9 @@ STATUS = {0: "CCG_OK", 1: "CCG_NOT_CONVERGED", -1: "CCG_ERR_INVALID", -2: "CCG_E
 OK, NOT_CONVERGED = 0, 1
 EXPORTED = ["ccg_config_init", "ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
             "ccg_block_product", "ccg_selftest_barrier_timeout", "ccg_status_string",
-            "ccg_version"]
+            "ccg_version", "ccg_lowp_create", "ccg_lowp_block_product", "ccg_lowp_bytes",
+            "ccg_lowp_destroy"]
+LOWP_BF16, LOWP_FP8_E4M3 = 0, 1
 
 
 class Config(ctypes.Structure):
@@ -73,8 +75,15 @@ def lib():
         L.ccg_status_string.restype = ctypes.c_char_p
         L.ccg_version.argtypes = []
         L.ccg_version.restype = ctypes.c_char_p
+        L.ccg_lowp_create.argtypes = [_VP, ctypes.c_int, _I64, _VP, _I64, ctypes.POINTER(_VP)]
+        L.ccg_lowp_block_product.argtypes = [_VP, _VP, _VP, ctypes.c_int, _VP,
+                                             ctypes.POINTER(ctypes.c_float)]
+        L.ccg_lowp_bytes.argtypes = [_VP]
+        L.ccg_lowp_bytes.restype = ctypes.c_int64
+        L.ccg_lowp_destroy.argtypes = [_VP]
         for name in ["ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
-                     "ccg_block_product", "ccg_selftest_barrier_timeout"]:
+                     "ccg_block_product", "ccg_selftest_barrier_timeout", "ccg_lowp_create",
+                     "ccg_lowp_block_product", "ccg_lowp_destroy"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -197,8 +206,47 @@ class Solver:
                                          _ptr(M), _ptr(G), ctypes.byref(ms))
         return rc, M, G, ms.value
 
+    def lowp_matrix(self, A, fmt: int, lda=None) -> "LowpMatrix":
+        """Quantised copy of A (ccg_lowp_create) on this handle's device."""
+        n = int(A.shape[0])
+        lda = int(A.shape[1]) if lda is None else lda
+        m = _VP()
+        rc = self._lib.ccg_lowp_create(self._h, int(fmt), n, _ptr(A), lda, ctypes.byref(m))
+        if rc != 0:
+            raise RuntimeError(f"ccg_lowp_create failed: {STATUS.get(rc, rc)}")
+        return LowpMatrix(self, m)
+
     def selftest_barrier_timeout(self, timeout_ms: float) -> int:
         return int(self._lib.ccg_selftest_barrier_timeout(self._h, float(timeout_ms)))
+
+
+class LowpMatrix:
+    """A quantised matrix (ccg_lowp_matrix); freed by close()."""
+
+    def __init__(self, solver: Solver, handle):
+        self._solver = solver
+        self._m = handle
+
+    def nbytes(self) -> int:
+        return int(self._solver._lib.ccg_lowp_bytes(self._m))
+
+    def block_product(self, V, W):
+        """W = A_lp V (ccg_lowp_block_product); returns (status, device_ms)."""
+        ms = ctypes.c_float(0.0)
+        rc = self._solver._lib.ccg_lowp_block_product(self._solver._h, self._m, _ptr(V),
+                                                      int(V.shape[1]), _ptr(W), ctypes.byref(ms))
+        return int(rc), ms.value
+
+    def close(self):
+        if getattr(self, "_m", None):
+            self._solver._lib.ccg_lowp_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def status_string(code: int) -> str:

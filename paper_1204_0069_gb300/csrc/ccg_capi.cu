@@ -11,96 +11,15 @@
 #include <new>
 
 #include "ccg.h"
+#include "ccg_handle.h"
 #include "ccg_internal.h"
 
 using ccg::DevState;
 using ccg::Params;
 
-struct ccg_handle_s {
-  ccg_config cfg;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  int num_sms = 0;
-  char* ws = nullptr;         // solver workspace
-  size_t ws_bytes = 0;
-  char* stage = nullptr;      // device copies of host inputs / outputs
-  size_t stage_bytes = 0;
-  DevState* h_state = nullptr;  // pinned host mirror of the device state
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
-
 namespace {
 
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
-int map_cuda(cudaError_t e) {
-  if (e == cudaSuccess) return CCG_OK;
-  if (e == cudaErrorMemoryAllocation) {
-    cudaGetLastError();
-    return CCG_ERR_OOM;
-  }
-  return CCG_ERR_CUDA;
-}
-
-bool is_device_ptr(const void* p) {
-  if (p == nullptr) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
-
-size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-int ensure(char** buf, size_t* have, size_t need) {
-  if (*have >= need) return CCG_OK;
-  if (*buf) {
-    cudaFree(*buf);
-    *buf = nullptr;
-    *have = 0;
-  }
-  const size_t sz = round_up(std::max<size_t>(need, 1), size_t(1) << 20);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(buf), sz);
-  if (e != cudaSuccess) {
-    *buf = nullptr;
-    return map_cuda(e);
-  }
-  *have = sz;
-  return CCG_OK;
-}
-
-// Bump allocator over a contiguous region (256-byte aligned pieces).
-struct Carve {
-  char* base;
-  size_t off = 0;
-  explicit Carve(char* b) : base(b) {}
-  template <class T>
-  T* take(size_t count) {
-    off = round_up(off, 256);
-    T* p = reinterpret_cast<T*>(base + off);
-    off += count * sizeof(T);
-    return p;
-  }
-  static size_t need(std::initializer_list<size_t> bytes) {
-    size_t o = 0;
-    for (size_t b : bytes) o = round_up(o, 256) + b;
-    return round_up(o, 256);
-  }
-};
+using namespace ccg_host;
 
 int grid_size(const ccg_handle_s* h, int64_t n) {
   int64_t g = std::min<int64_t>(h->num_sms, (n + ccg::kWarps - 1) / ccg::kWarps);

@@ -1,0 +1,45 @@
+// ccg_lowp.h -- internal interface of the tensor-core low-precision block
+// product (ccg_lowp.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ccg {
+namespace lp {
+
+enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1 };
+
+// Launch description of one stream-K block product.
+struct LpRun {
+  int64_t n;               // rows = columns of A
+  int64_t units;           // row tiles x k-chunks
+  int kc;                  // k-chunks per row tile
+  int k_elems;             // K elements per chunk (128 bytes)
+  int ctas;                // grid size
+  int pad;
+  float* part;             // partial tiles, part_floats(n, ctas, NP) floats
+  int* error;              // device error flag (0 = ok, -5 = wait timed out)
+  long long timeout_ns;    // mbarrier wait limit
+  const float* row_scale;  // FP8: per-row scale of A (else NULL)
+  const float* col_scale;  // FP8: per-column scale of D (else NULL)
+};
+
+// Leading dimension (elements) of a quantised operand row: n rounded up to 128.
+int64_t ld_elems(int64_t n);
+// Floats of partial-tile storage for a launch on `ctas` CTAs with N = NP.
+size_t part_floats(int64_t n, int ctas, int NP);
+// A (FP64) -> Q: BF16, or FP8 E4M3 with per-row scales (row_scale, n floats).
+cudaError_t quantize(int kind, const double* A, int64_t lda, int64_t n, void* Q, int64_t ldq,
+                     float* row_scale, cudaStream_t s);
+// V (FP64, n x q row-major) -> Vt: NP (BF16) or 2 NP (FP8 hi, lo) rows of ldk
+// elements, K contiguous; FP8 also writes the column scales (cmax: 32 uints).
+cudaError_t convert_operand(int kind, const double* V, int64_t n, int q, int NP, void* Vt,
+                            int64_t ldk, unsigned int* cmax, float* col_scale, cudaStream_t s);
+// W (FP64, n x q) = A_lp V_lp; events (optional) bracket the two kernels.
+cudaError_t block_product(int kind, int NP, const void* Q, int64_t ldq, const void* Vt,
+                          int64_t ldk, LpRun run, int q, double* W, cudaStream_t s,
+                          cudaEvent_t ev0, cudaEvent_t ev1);
+
+}  // namespace lp
+}  // namespace ccg
