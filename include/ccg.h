@@ -192,6 +192,41 @@ int64_t ccg_lowp_bytes(const ccg_lowp_matrix* m);
 /* Free the quantised matrix.  NULL-safe. */
 int ccg_lowp_destroy(ccg_lowp_matrix* m);
 
+/* ---- Solve without any device allocation --------------------------------- */
+
+/* Largest n * p accepted by ccg_solve_noalloc. */
+#define CCG_NOALLOC_MAX_NP 131072
+
+/*
+ * ccg_solve without a handle and without allocating: no cudaMalloc, no
+ * cudaFree, no pinned host buffer, no events.  The paper has no counterpart;
+ * this entry exists for callers that cannot allocate device memory on the
+ * fly -- for instance a process whose device memory is owned by its own
+ * pool allocator or budget, or a latency-bound loop that cannot afford the
+ * synchronisation an allocation may cause.
+ *
+ * All pointers (A, b, x0, x_out) must be device memory on `device`; host
+ * pointers are rejected.  The solve runs on `stream` (NULL = legacy default
+ * stream) with the default configuration of ccg_config_init (x0 spread 1,
+ * seed 0, rank_tol 1e-12, residual replacement on, 10 s barrier limit) and
+ * returns after the result is on the host.  res->device_ms is 0 (no events).
+ *
+ * Scratch: one file-scope device array of about 10.7 MB (5 blocks of
+ * CCG_NOALLOC_MAX_NP doubles, per-CTA partial sums for up to 160 CTAs and the
+ * solver state), held by every GPU that loads the library until the process
+ * exits.  The first call on a device looks up the array's device address (a
+ * runtime symbol lookup); make that first call before any stream capture.
+ * Every call on a device shares the same array, so calls that overlap on the
+ * GPU race: serialise them (one stream, or wait between calls).  The solver
+ * state is cleared on every call.
+ *
+ * Errors: CCG_ERR_INVALID for arguments ccg_solve rejects, for host
+ * pointers, and for n * p > CCG_NOALLOC_MAX_NP; otherwise as ccg_solve.
+ */
+int ccg_solve_noalloc(int device, void* stream, int64_t n, const double* A, int64_t lda,
+                      const double* b, const double* x0, int p, double tol, int maxit,
+                      double* x_out, ccg_result* res);
+
 /* Name of a status code ("CCG_OK", ...). */
 const char* ccg_status_string(int status);
 

@@ -22,7 +22,8 @@ OK, NOT_CONVERGED = 0, 1
 EXPORTED = ["ccg_config_init", "ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
             "ccg_block_product", "ccg_selftest_barrier_timeout", "ccg_status_string",
             "ccg_version", "ccg_lowp_create", "ccg_lowp_block_product", "ccg_lowp_bytes",
-            "ccg_lowp_destroy"]
+            "ccg_lowp_destroy", "ccg_solve_noalloc"]
+NOALLOC_MAX_NP = 131072
 LOWP_BF16, LOWP_FP8_E4M3 = 0, 1
 
 
@@ -81,6 +82,9 @@ def lib():
         L.ccg_lowp_bytes.argtypes = [_VP]
         L.ccg_lowp_bytes.restype = ctypes.c_int64
         L.ccg_lowp_destroy.argtypes = [_VP]
+        L.ccg_solve_noalloc.argtypes = [ctypes.c_int, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_int, _VP, ctypes.POINTER(Result)]
+        L.ccg_solve_noalloc.restype = ctypes.c_int
         for name in ["ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
                      "ccg_block_product", "ccg_selftest_barrier_timeout", "ccg_lowp_create",
                      "ccg_lowp_block_product", "ccg_lowp_destroy"]:
@@ -247,6 +251,18 @@ class LowpMatrix:
             self.close()
         except Exception:
             pass
+
+
+def solve_noalloc(A, b, x_out, p: int, tol: float, maxit: int, x0=None, device: int = 0,
+                  stream=None, lda=None) -> SolveResult:
+    """ccg_solve_noalloc: a solve that allocates nothing (device tensors only;
+    its scratch is a fixed device array, so calls must not overlap)."""
+    n = int(b.shape[0])
+    lda = int(A.shape[1]) if lda is None else lda
+    r = Result()
+    lib().ccg_solve_noalloc(int(device), stream, n, _ptr(A), lda, _ptr(b), _ptr(x0), int(p),
+                            float(tol), int(maxit), _ptr(x_out), ctypes.byref(r))
+    return Solver._res(r)
 
 
 def status_string(code: int) -> str:
