@@ -56,7 +56,9 @@ typedef enum {
 } ccg_status;
 
 typedef enum {
-    CCG_FP64 = 0             /* every operation in FP64                      */
+    CCG_FP64 = 0,            /* every operation in FP64                      */
+    CCG_BF16_IR = 2,         /* A in BF16 on the tensor cores, FP64 refinement */
+    CCG_FP8_IR = 3           /* A in FP8 E4M3 on the tensor cores, FP64 refinement */
 } ccg_precision;
 
 typedef struct {
@@ -71,6 +73,9 @@ typedef struct {
                                    tol, restart from R = A X - b 1' (default)*/
     double barrier_timeout_ms;  /* in-kernel barrier wait limit; 10000 ms    */
     int max_ctas;               /* 0 = one CTA per SM; else an upper bound   */
+    double inner_tol;           /* mixed precision: relative tolerance of each
+                                   inner solve; 0 = 1e-2 (BF16), 1e-1 (FP8)  */
+    int max_outer;              /* mixed precision: refinement steps; 0 = 60 */
 } ccg_config;
 
 typedef struct {
@@ -84,6 +89,7 @@ typedef struct {
     double relres_recur;  /* min_j ||R e_j|| / ||b|| from the recurrence      */
     float device_ms;      /* device time of the solve kernel(s)               */
     int ctas;             /* CTAs of the persistent launch                    */
+    int outer_steps;      /* mixed precision: refinement steps taken          */
 } ccg_result;
 
 /* Fill *cfg with the defaults listed above. */
@@ -116,6 +122,8 @@ int ccg_destroy(ccg_handle* handle);
  *               returned agent, ||b - A x||/||b|| in FP64, is <= tol.
  *   maxit     : maximum cCG iterations (>= 0).
  *   x_out     : n values; receives the agent with the smallest residual.
+ * With cfg.precision CCG_BF16_IR or CCG_FP8_IR the call quantises A into a
+ * handle-owned copy and runs ccg_solve_mixed (see there).
  *   res       : optional result record (host memory).
  * Errors: CCG_ERR_INVALID (n < 1, p out of range, tol <= 0, maxit < 0,
  * lda < n, NULL pointer), CCG_ERR_NOT_SPD, CCG_ERR_NUMERICAL, CCG_ERR_OOM,
@@ -185,6 +193,24 @@ int ccg_lowp_create(ccg_handle* handle, int format, int64_t n, const double* A, 
  */
 int ccg_lowp_block_product(ccg_handle* handle, const ccg_lowp_matrix* m, const double* V, int q,
                            double* W, float* device_ms);
+
+/*
+ * Mixed-precision solve of A x = b (FP64 result): iterative refinement in
+ * FP64 around inner cCG solves whose block products use the quantised copy
+ * `lpA` of A on the tensor cores.  Each step computes the FP64 residual
+ * r = b - A x, solves A_lp d = r with p agents to the relative tolerance
+ * cfg.inner_tol (the recurrence residual decides), and updates x += d.  The
+ * solve stops when ||b - A x|| / ||b|| <= tol (CCG_OK), or returns the best x
+ * with CCG_NOT_CONVERGED when maxit inner iterations or cfg.max_outer steps
+ * are used up, two steps in a row fail to improve the residual, or an inner
+ * solve breaks down (A_lp not positive definite) -- refinement contracts only
+ * when A_lp approximates A well enough for the system's conditioning.  x0 may be NULL (zeros).  res->iterations counts inner
+ * iterations, res->outer_steps refinement steps, res->relres_true is the FP64
+ * relative residual of x_out.  lpA must have been made from this A.
+ */
+int ccg_solve_mixed(ccg_handle* handle, const ccg_lowp_matrix* lpA, int64_t n, const double* A,
+                    int64_t lda, const double* b, const double* x0, int p, double tol,
+                    int maxit, double* x_out, ccg_result* res);
 
 /* Bytes of device memory held by the quantised matrix (entries + scales). */
 int64_t ccg_lowp_bytes(const ccg_lowp_matrix* m);

@@ -22,7 +22,8 @@ OK, NOT_CONVERGED = 0, 1
 EXPORTED = ["ccg_config_init", "ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
             "ccg_block_product", "ccg_selftest_barrier_timeout", "ccg_status_string",
             "ccg_version", "ccg_lowp_create", "ccg_lowp_block_product", "ccg_lowp_bytes",
-            "ccg_lowp_destroy", "ccg_solve_noalloc"]
+            "ccg_lowp_destroy", "ccg_solve_noalloc", "ccg_solve_mixed"]
+FP64, BF16_IR, FP8_IR = 0, 2, 3
 NOALLOC_MAX_NP = 131072
 LOWP_BF16, LOWP_FP8_E4M3 = 0, 1
 
@@ -32,7 +33,8 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("rank_tol", ctypes.c_double),
                 ("x0_spread", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("residual_replacement", ctypes.c_int),
-                ("barrier_timeout_ms", ctypes.c_double), ("max_ctas", ctypes.c_int)]
+                ("barrier_timeout_ms", ctypes.c_double), ("max_ctas", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -40,7 +42,8 @@ class Result(ctypes.Structure):
                 ("agent", ctypes.c_int), ("p_final", ctypes.c_int),
                 ("replacements", ctypes.c_int), ("drops", ctypes.c_int),
                 ("relres_true", ctypes.c_double), ("relres_recur", ctypes.c_double),
-                ("device_ms", ctypes.c_float), ("ctas", ctypes.c_int)]
+                ("device_ms", ctypes.c_float), ("ctas", ctypes.c_int),
+                ("outer_steps", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -85,6 +88,9 @@ def lib():
         L.ccg_solve_noalloc.argtypes = [ctypes.c_int, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_int, _VP, ctypes.POINTER(Result)]
         L.ccg_solve_noalloc.restype = ctypes.c_int
+        L.ccg_solve_mixed.argtypes = [_VP, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, _VP, ctypes.POINTER(Result)]
+        L.ccg_solve_mixed.restype = ctypes.c_int
         for name in ["ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
                      "ccg_block_product", "ccg_selftest_barrier_timeout", "ccg_lowp_create",
                      "ccg_lowp_block_product", "ccg_lowp_destroy"]:
@@ -132,6 +138,7 @@ class SolveResult:
     relres_recur: float
     device_ms: float
     ctas: int
+    outer_steps: int
 
 
 class Solver:
@@ -139,7 +146,8 @@ class Solver:
 
     def __init__(self, device: int = 0, stream=None, rank_tol: float = 1e-12,
                  x0_spread: float = 1.0, seed: int = 0, residual_replacement: bool = True,
-                 barrier_timeout_ms: float = 10000.0, max_ctas: int = 0):
+                 barrier_timeout_ms: float = 10000.0, max_ctas: int = 0, precision: int = 0,
+                 inner_tol: float = 0.0, max_outer: int = 0):
         L = lib()
         cfg = Config()
         L.ccg_config_init(ctypes.byref(cfg))
@@ -151,6 +159,9 @@ class Solver:
         cfg.residual_replacement = int(bool(residual_replacement))
         cfg.barrier_timeout_ms = barrier_timeout_ms
         cfg.max_ctas = max_ctas
+        cfg.precision = precision
+        cfg.inner_tol = inner_tol
+        cfg.max_outer = max_outer
         h = _VP()
         rc = L.ccg_create(ctypes.byref(h), ctypes.byref(cfg))
         if rc != 0:
@@ -209,6 +220,16 @@ class Solver:
         rc = self._lib.ccg_block_product(self._h, n, _ptr(A), lda, _ptr(V), _ptr(U), q, _ptr(W),
                                          _ptr(M), _ptr(G), ctypes.byref(ms))
         return rc, M, G, ms.value
+
+    def solve_mixed(self, lpA: "LowpMatrix", A, b, x_out, p: int, tol: float, maxit: int,
+                    x0=None, lda=None) -> SolveResult:
+        """ccg_solve_mixed: FP64 refinement around inner solves on lpA."""
+        n = int(b.shape[0])
+        lda = int(A.shape[1]) if lda is None else lda
+        r = Result()
+        self._lib.ccg_solve_mixed(self._h, lpA._m, n, _ptr(A), lda, _ptr(b), _ptr(x0), int(p),
+                                  float(tol), int(maxit), _ptr(x_out), ctypes.byref(r))
+        return self._res(r)
 
     def lowp_matrix(self, A, fmt: int, lda=None) -> "LowpMatrix":
         """Quantised copy of A (ccg_lowp_create) on this handle's device."""

@@ -204,6 +204,8 @@ void ccg_config_init(ccg_config* cfg) {
   cfg->residual_replacement = 1;
   cfg->barrier_timeout_ms = 10000.0;
   cfg->max_ctas = 0;
+  cfg->inner_tol = 0.0;
+  cfg->max_outer = 0;
 }
 
 int ccg_create(ccg_handle** out, const ccg_config* cfg) {
@@ -212,8 +214,9 @@ int ccg_create(ccg_handle** out, const ccg_config* cfg) {
   ccg_config c;
   if (cfg) c = *cfg;
   else ccg_config_init(&c);
-  if (!(c.rank_tol > 0.0) || !(c.barrier_timeout_ms > 0.0) || c.precision != CCG_FP64 ||
-      c.max_ctas < 0)
+  if (!(c.rank_tol > 0.0) || !(c.barrier_timeout_ms > 0.0) ||
+      (c.precision != CCG_FP64 && c.precision != CCG_BF16_IR && c.precision != CCG_FP8_IR) ||
+      c.max_ctas < 0 || c.inner_tol < 0.0 || c.max_outer < 0)
     return CCG_ERR_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -250,12 +253,28 @@ int ccg_destroy(ccg_handle* h) {
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
   }
+  if (h->lp) ccg_lowp_destroy(h->lp);
   delete h;
   return CCG_OK;
 }
 
 int ccg_solve(ccg_handle* h, int64_t n, const double* A, int64_t lda, const double* b,
               const double* x0, int p, double tol, int maxit, double* x_out, ccg_result* res) {
+  if (h && h->cfg.precision != CCG_FP64) {
+    // mixed precision: quantise A into the handle's copy, then refine in FP64
+    if (h->lp) {
+      ccg_lowp_destroy(h->lp);
+      h->lp = nullptr;
+    }
+    const int fmt = h->cfg.precision == CCG_BF16_IR ? CCG_LOWP_BF16 : CCG_LOWP_FP8_E4M3;
+    if (res) std::memset(res, 0, sizeof(*res));
+    const int rc = ccg_lowp_create(h, fmt, n, A, lda, &h->lp);
+    if (rc != CCG_OK) {
+      if (res) res->status = rc;
+      return rc;
+    }
+    return ccg_solve_mixed(h, h->lp, n, A, lda, b, x0, p, tol, maxit, x_out, res);
+  }
   return solve_impl(h, n, A, lda, b, x0, nullptr, p, tol, maxit, x_out, nullptr, res);
 }
 

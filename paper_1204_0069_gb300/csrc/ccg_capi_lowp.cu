@@ -12,15 +12,6 @@
 
 using namespace ccg_host;
 
-struct ccg_lowp_matrix_s {
-  int format = 0;
-  int device = 0;
-  int64_t n = 0;
-  int64_t ldq = 0;
-  void* q = nullptr;          // n x ldq entries
-  float* row_scale = nullptr; // FP8: n scales
-  int64_t bytes = 0;
-};
 
 namespace {
 

@@ -12,6 +12,16 @@
 #include "ccg.h"
 #include "ccg_internal.h"
 
+struct ccg_lowp_matrix_s {
+  int format = 0;
+  int device = 0;
+  int64_t n = 0;
+  int64_t ldq = 0;
+  void* q = nullptr;          // n x ldq entries
+  float* row_scale = nullptr; // FP8: n scales
+  int64_t bytes = 0;
+};
+
 struct ccg_handle_s {
   ccg_config cfg;
   cudaStream_t stream = nullptr;
@@ -23,6 +33,7 @@ struct ccg_handle_s {
   size_t stage_bytes = 0;
   ccg::DevState* h_state = nullptr;  // pinned host mirror of the device state
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  ccg_lowp_matrix_s* lp = nullptr;  // quantised copy made by ccg_solve (mixed precision)
 };
 
 namespace ccg_host {

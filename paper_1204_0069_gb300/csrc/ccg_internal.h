@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace ccg {
@@ -33,8 +34,13 @@ enum Ctrl : int {
 enum Mode : int {
   MODE_SOLVE = 0,
   MODE_BLOCK_PRODUCT = 1,
-  MODE_BARRIER_SELFTEST = 2
+  MODE_BARRIER_SELFTEST = 2,
+  MODE_REFINE = 3      // x += c delta; r = b - A x (FP64); scaled residual
 };
+
+// A-pass policy of the persistent kernel: FP64 A on the FP64 pipe, or a
+// quantised A on the tensor cores (inner solves of the mixed-precision path).
+enum Policy : int { POL_FP64 = 0, POL_BF16 = 1, POL_FP8 = 2 };
 
 // Status values mirror ccg_status in include/ccg.h.
 enum Status : int {
@@ -78,6 +84,8 @@ struct DevState {
   double alphaT[kSq];       // (alpha_k^T)[b][a], stride kMaxP
   double betaT[kSq];        // (beta_k^T)[b][a], stride kMaxP
   double gram_out[2 * kSq]; // block-product mode: M, G (stride kMaxP)
+  float sigma[kMaxP];       // FP8 operand column scales
+  double rnorm;             // refinement mode: ||b - A x||
 };
 
 struct Params {
@@ -111,16 +119,34 @@ struct Params {
   const double* U;
   double* Wout;
   int q;
+  // inner solves (mixed precision): stop on the recurrence residual alone
+  int skip_true_check;
+  // tensor-core A-pass (policy != POL_FP64)
+  int lp_kc;               // k-chunks per 128-row tile
+  int lp_kelems;           // K elements per chunk
+  int64_t lp_units;        // row tiles x k-chunks
+  const float* lp_row_scale;
+  void* lp_dq;             // quantised operand rows (NB x lp_ldk)
+  int64_t lp_ldk;
+  float* lp_part;          // partial tiles, (grid + tiles) x 128 x NP floats
+  // refinement mode
+  double* ref_x;
+  const double* ref_delta;
+  double ref_coef;
+  double* ref_r;           // A x - b
+  double* ref_bin;         // -(A x - b) * sqrt(n) / ||b - A x||
+  alignas(64) CUtensorMap lp_tmA;  // A_lp tiles
+  alignas(64) CUtensorMap lp_tmB;  // operand tiles
 };
 
 // Launch helpers implemented in ccg_fp64.cu.
 // Bucket (1, 2, 4, 8, 16, 32) >= p used for the register tiles.
 int p_bucket(int p);
-// Dynamic shared memory the kernel needs for bucket P.
-size_t fp64_smem_bytes(int P);
-// Max co-resident CTAs per SM of the FP64 kernel (0 on error).
-int fp64_ctas_per_sm(int P, bool vec);
+// Dynamic shared memory the kernel needs for bucket P and policy pol.
+size_t fp64_smem_bytes(int P, int pol = POL_FP64);
+// Max co-resident CTAs per SM of the persistent kernel (0 on error).
+int fp64_ctas_per_sm(int P, bool vec, int pol = POL_FP64);
 cudaError_t launch_fp64(const Params& prm, int P, bool vec, int ctas,
-                        cudaStream_t stream);
+                        cudaStream_t stream, int pol = POL_FP64);
 
 }  // namespace ccg

@@ -32,155 +32,14 @@
 #include <cstdint>
 
 #include "ccg_lowp.h"
+#include "ccg_tc.cuh"
 
 namespace ccg {
 namespace lp {
 namespace {
 
-constexpr int kBM = 128;          // rows per tile (MMA M)
-constexpr int kRowBytes = 128;    // K bytes per stage = one 128-byte swizzle atom
-constexpr int kStages = 6;
+using namespace ccg::tc;
 constexpr int kThreadsLp = 192;
-constexpr int kTileABytes = kBM * kRowBytes;  // 16 KB
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// ---- mbarrier --------------------------------------------------------------
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok) : "r"(a), "r"(parity) : "memory");
-  return ok != 0;
-}
-// Bounded wait: false (and the error flag set) after timeout_ns.
-__device__ bool mbar_wait(uint32_t a, uint32_t parity, long long timeout_ns, int* err) {
-  for (int i = 0; i < 128; ++i)
-    if (mbar_try(a, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  while (!mbar_try(a, parity)) {
-    if (*(volatile int*)err != 0) return false;
-    if (gtimer() - t0 > (unsigned long long)timeout_ns) {
-      atomicCAS(err, 0, -5);
-      return false;
-    }
-    __nanosleep(64);
-  }
-  return true;
-}
-
-// ---- TMA -------------------------------------------------------------------
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y,
-                                            uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
-
-// ---- tcgen05 ---------------------------------------------------------------
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
-  return d;
-}
-template <int KIND>
-__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
-                                    uint32_t accum) {
-  if constexpr (KIND == KIND_BF16) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
-        : "memory");
-  }
-}
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-      : "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N.
-template <int KIND>
-__host__ __device__ constexpr uint32_t idesc(int N) {
-  return (1u << 4)                                  // D format F32
-         | ((KIND == KIND_BF16 ? 1u : 0u) << 7)     // A format: BF16 / E4M3
-         | ((KIND == KIND_BF16 ? 1u : 0u) << 10)    // B format: BF16 / E4M3
-         | ((uint32_t)(N >> 3) << 17)               // N / 8
-         | ((uint32_t)(kBM >> 4) << 24);            // M / 16
-}
-
-// 32 lanes x N columns of FP32 from tensor memory.
-template <int N>
-__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]) {
-  uint32_t r[N];
-  if constexpr (N == 16) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-  } else {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-  }
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < N; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Stream-K range of CTA c over U units on G CTAs.
-__host__ __device__ __forceinline__ int64_t unit_begin(int64_t U, int G, int c) {
-  return (U * c) / G;
-}
 
 // ---- the block-product kernel ----------------------------------------------
 template <int KIND, int NP>
@@ -496,6 +355,11 @@ bool make_map(CUtensorMap* m, const void* base, int kind, int64_t rows, int64_t 
 }
 
 }  // namespace
+
+bool make_tensor_map(CUtensorMap* m, const void* base, int kind, int64_t rows, int64_t cols,
+                     int64_t ld, int box_rows) {
+  return make_map(m, base, kind, rows, cols, ld, box_rows);
+}
 
 int64_t ld_elems(int64_t n) { return (n + 127) / 128 * 128; }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace ccg {
@@ -36,6 +37,10 @@ cudaError_t quantize(int kind, const double* A, int64_t lda, int64_t n, void* Q,
 // elements, K contiguous; FP8 also writes the column scales (cmax: 32 uints).
 cudaError_t convert_operand(int kind, const double* V, int64_t n, int q, int NP, void* Vt,
                             int64_t ldk, unsigned int* cmax, float* col_scale, cudaStream_t s);
+// 2-D TMA tensor map over a rows x cols operand (K contiguous, ld elements),
+// box of box_rows x 128 bytes, 128-byte swizzle.
+bool make_tensor_map(CUtensorMap* m, const void* base, int kind, int64_t rows, int64_t cols,
+                     int64_t ld, int box_rows);
 // W (FP64, n x q) = A_lp V_lp; events (optional) bracket the two kernels.
 cudaError_t block_product(int kind, int NP, const void* Q, int64_t ldq, const void* Vt,
                           int64_t ldk, LpRun run, int q, double* W, cudaStream_t s,

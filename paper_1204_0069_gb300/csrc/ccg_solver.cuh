@@ -1,0 +1,1374 @@
+// ccg_solver.cuh -- the persistent solver kernel for the cooperative conjugate
+// gradient method (cCG, Algorithm 2 of arXiv:1204.0069) with the deflation of
+// Algorithm 3 (mcCG) and the stopping rule of Algorithm 4.
+//
+// One cooperative launch runs a whole solve.  CTA c owns rows
+// [c n / G, (c+1) n / G) of A, X, R, D and W = A D.  Each iteration is the
+// sequence of Table 1 with its two exchange points, plus one barrier before
+// the next block product:
+//
+//   A-pass   W = A D_k (own rows; A streamed once per iteration), and the
+//            per-CTA partials of M = D'W, G = R'D           (Table 1, rows 1-3)
+//   sync #1  last-arriving CTA: fixed-order sum of the partials, scaled
+//            Cholesky of M with the rank test of Algorithm 3, alpha_k
+//   update   X += D alpha^T, R += W alpha^T (recurrence, proof of Thm. 2);
+//            partials of H = R_{k+1}'W and ||R_{k+1} e_j||^2  (Table 1, rows 5-7)
+//   sync #2  last-arriving CTA: beta_k, stop test min_j ||R e_j|| <= tol ||b||
+//   D-update D_{k+1} = R_{k+1} + D_k beta^T                  (Table 1, row 9)
+//   barrier
+//
+// The p x p Grams and the norms are inner products that the method treats as
+// exact (Sec. 4 works in exact arithmetic); they decide the matrix stepsizes
+// and the stop test, so they are accumulated with error-free transformations
+// (Dot2 of Ogita, Rump and Oishi 2005: exact products by FMA, TwoSum for the
+// running sum) per CTA and again across CTAs.  All cross-CTA sums run in a
+// fixed order (CTA 0, 1, ...), so a solve is bitwise reproducible for a fixed
+// grid.  Every wait on another CTA gives up
+// after Params::timeout_ns and sets CCG_ERR_TIMEOUT; all CTAs then return.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "ccg_internal.h"
+#include "ccg_tc.cuh"
+
+namespace ccg {
+namespace {
+
+// --------------------------------------------------------------------------
+// Memory-model helpers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+               : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Cross-CTA data produced inside the launch is read through L2 only.
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
+
+__device__ void set_error(DevState* st, int code, int where) {
+  if (atomicCAS(&st->error, 0, code) == 0) st->err_where = where;
+}
+
+// Compensated accumulation (Dot2).  The intrinsics keep the compiler from
+// contracting the error-free transformations into FMAs.
+struct DSum {
+  double hi;
+  double lo;
+};
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  const double z = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, z)), __dsub_rn(b, z));
+}
+__device__ __forceinline__ void dsum_fma(DSum& t, double x, double y) {
+  const double p = __dmul_rn(x, y);
+  const double pe = fma(x, y, -p);  // exact product error
+  double s, e;
+  two_sum(t.hi, p, s, e);
+  t.hi = s;
+  t.lo = __dadd_rn(t.lo, __dadd_rn(pe, e));
+}
+__device__ __forceinline__ void dsum_add(DSum& t, double hi, double lo) {
+  double s, e;
+  two_sum(t.hi, hi, s, e);
+  t.hi = s;
+  t.lo = __dadd_rn(t.lo, __dadd_rn(lo, e));
+}
+// Warp-wide compensated sum in a fixed butterfly order; all lanes get it.
+__device__ __forceinline__ DSum dsum_warp(DSum t) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    const double oh = __shfl_xor_sync(0xffffffffu, t.hi, m);
+    const double ol = __shfl_xor_sync(0xffffffffu, t.lo, m);
+    // combine in lane order so both partners compute the same value
+    const bool low = (threadIdx.x & m) == 0;
+    DSum a = low ? t : DSum{oh, ol};
+    const DSum b = low ? DSum{oh, ol} : t;
+    dsum_add(a, b.hi, b.lo);
+    t = a;
+  }
+  return t;
+}
+
+// --------------------------------------------------------------------------
+// Grid synchronisation with an optional serial step.
+//   grid_arrive: 1 = this CTA arrived last and must run the serial step and
+//   then grid_release; 0 = released (serial step complete and visible);
+//   -1 = an error is set or the wait timed out: leave the kernel.
+// --------------------------------------------------------------------------
+struct SyncShared {
+  unsigned gen;
+  int flag;
+};
+
+__device__ int grid_arrive(const Params& prm, SyncShared* ss) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DevState* st = prm.st;
+    __threadfence();
+    const unsigned gen = ld_acquire_u32(&st->bar_gen);
+    const unsigned arrived = atom_add_acqrel_u32(&st->bar_count, 1u);
+    int flag;
+    if (arrived == prm.expected_ctas - 1u) {
+      flag = 1;
+      __threadfence();
+    } else {
+      flag = 0;
+      const unsigned long long t0 = globaltimer_ns();
+      while (ld_acquire_u32(&st->bar_gen) == gen) {
+        if (*(volatile int*)&st->error != 0) { flag = -1; break; }
+        if (globaltimer_ns() - t0 > (unsigned long long)prm.timeout_ns) {
+          set_error(st, ST_ERR_TIMEOUT, 100);
+          flag = -1;
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+    }
+    if (flag == 0 && *(volatile int*)&st->error != 0) flag = -1;
+    ss->gen = gen;
+    ss->flag = flag;
+  }
+  __syncthreads();
+  return ss->flag;
+}
+
+__device__ void grid_release(const Params& prm, SyncShared* ss) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(&prm.st->bar_count, 0u);
+    st_release_u32(&prm.st->bar_gen, ss->gen + 1u);
+  }
+  __syncthreads();
+}
+
+// Error state broadcast to the whole CTA (one read, uniform decision).
+__device__ __forceinline__ bool cta_error(const DevState* st, int* s_err) {
+  __syncthreads();
+  if (threadIdx.x == 0) *s_err = *(volatile const int*)&st->error;
+  __syncthreads();
+  return *s_err != 0;
+}
+
+// Plain barrier; false = leave the kernel.
+__device__ bool grid_barrier(const Params& prm, SyncShared* ss, int* s_err) {
+  const int f = grid_arrive(prm, ss);
+  if (f < 0) return false;
+  if (f == 1) grid_release(prm, ss);
+  return !cta_error(prm.st, s_err);
+}
+
+// --------------------------------------------------------------------------
+// Block product tile shapes.  Lanes of a warp split the k range of one row
+// of A (two consecutive k per lane, 16-byte loads); a k-chunk of the operand
+// V (BK x P) is staged transposed in shared memory and shared by the CTA's 8
+// rows of the pass.  The next chunk's A values (registers) and V values
+// (registers, then the second shared buffer) are fetched while the current
+// chunk is multiplied, so each chunk costs one CTA barrier and the memory
+// latency hides behind the FP64 pipe.  NS independent accumulator sets keep
+// >= 8 FMA chains per lane.
+// --------------------------------------------------------------------------
+template <int P>
+struct Tile {
+  static constexpr int BK = (2048 / P < 512) ? 2048 / P : 512;
+  static constexpr int VSTR = BK + 2;          // padded shared row (16-byte aligned)
+  static constexpr int NS = (P >= 8) ? 1 : 8 / P;
+  static constexpr int NLD = BK / 64;          // double2 loads of A per lane per chunk
+  static constexpr int NV = BK * P / kThreads; // staged V values per thread per chunk
+  static constexpr int LOGP = (P == 1) ? 0 : (P == 2) ? 1 : (P == 4) ? 2
+                             : (P == 8) ? 3 : (P == 16) ? 4 : 5;
+  static_assert(NV >= 1 && NV * kThreads == BK * P, "chunk must tile the CTA");
+};
+
+// Reduce-scatter over the 32 lanes: afterwards v[0] holds, in every lane, the
+// full sum of column (lane >> (5 - log2 P)).
+template <int CNT, int M>
+struct ReduceScatter {
+  __device__ __forceinline__ static void run(double* v, int lane) {
+    if constexpr (CNT > 1) {
+      constexpr int H = CNT / 2;
+      const bool up = (lane & M) != 0;
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        const double send = up ? v[i] : v[i + H];
+        const double keep = up ? v[i + H] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, M);
+      }
+      if constexpr (M > 1) ReduceScatter<H, M / 2>::run(v, lane);
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], M);
+      if constexpr (M > 1) ReduceScatter<1, M / 2>::run(v, lane);
+    }
+  }
+};
+
+template <int P>
+__device__ __forceinline__ void load_v_chunk(const double* __restrict__ V, int ldv, int coff,
+                                             int pk, int64_t n, int64_t k0, double (&v)[Tile<P>::NV]) {
+#pragma unroll
+  for (int t = 0; t < Tile<P>::NV; ++t) {
+    const int idx = threadIdx.x + t * kThreads;
+    const int kk = idx >> Tile<P>::LOGP;
+    const int c = idx & (P - 1);
+    const int64_t k = k0 + kk;
+    v[t] = (c < pk && k < n) ? ldcg(V + k * ldv + coff + c) : 0.0;
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void store_v_chunk(double* Vb, const double (&v)[Tile<P>::NV]) {
+#pragma unroll
+  for (int t = 0; t < Tile<P>::NV; ++t) {
+    const int idx = threadIdx.x + t * kThreads;
+    Vb[(idx & (P - 1)) * Tile<P>::VSTR + (idx >> Tile<P>::LOGP)] = v[t];
+  }
+}
+
+template <int P, bool VEC>
+__device__ __forceinline__ void load_a_chunk(const double* Arow, int64_t n, int64_t k0, int lane,
+                                             bool valid, double2 (&a)[Tile<P>::NLD]) {
+#pragma unroll
+  for (int j = 0; j < Tile<P>::NLD; ++j) {
+    const int64_t k = k0 + j * 64 + 2 * lane;
+    double2 v = make_double2(0.0, 0.0);
+    if (valid) {
+      if (VEC && k + 1 < n) {
+        v = __ldcs(reinterpret_cast<const double2*>(Arow + k));
+      } else {
+        if (k < n) v.x = __ldcs(Arow + k);
+        if (k + 1 < n) v.y = __ldcs(Arow + k + 1);
+      }
+    }
+    a[j] = v;
+  }
+}
+
+// Y[row, c] = sum_k A[row, k] V[k, coff + c] (- b[row]) for the rows
+// [r0, r1) and c < pk.  Vs: shared scratch of 2 * P * VSTR doubles.
+template <int P, bool VEC>
+__device__ void apass(const Params& prm, const double* __restrict__ V, int ldv,
+                      int coff, int pk, double* __restrict__ Y, int ldy,
+                      bool sub_b, int64_t r0, int64_t r1, double* Vs) {
+  using T = Tile<P>;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t n = prm.n;
+  const int64_t lda = prm.lda;
+  const int64_t nr = r1 - r0;
+  const int64_t w0 = r0 + (nr * warp) / kWarps;
+  const int64_t w1 = r0 + (nr * (warp + 1)) / kWarps;
+  const int64_t passes = (nr + kWarps - 1) / kWarps;
+  const int64_t nch = (n + T::BK - 1) / T::BK;
+  const double* __restrict__ A = prm.A;
+
+  for (int64_t ps = 0; ps < passes; ++ps) {
+    const int64_t row = w0 + ps;
+    const bool valid = row < w1;
+    const double* Arow = A + (valid ? row : r0) * lda;
+    double acc[T::NS][P];
+#pragma unroll
+    for (int s = 0; s < T::NS; ++s)
+#pragma unroll
+      for (int c = 0; c < P; ++c) acc[s][c] = 0.0;
+
+    double vreg[T::NV];
+    double2 acur[T::NLD], anxt[T::NLD];
+    load_v_chunk<P>(V, ldv, coff, pk, n, 0, vreg);
+    load_a_chunk<P, VEC>(Arow, n, 0, lane, valid, acur);
+    store_v_chunk<P>(Vs, vreg);
+    __syncthreads();
+    for (int64_t ch = 0; ch < nch; ++ch) {
+      const bool more = ch + 1 < nch;
+      if (more) {
+        load_v_chunk<P>(V, ldv, coff, pk, n, (ch + 1) * T::BK, vreg);
+        load_a_chunk<P, VEC>(Arow, n, (ch + 1) * T::BK, lane, valid, anxt);
+      }
+      const double* Vb = Vs + (ch & 1) * (P * T::VSTR);
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < T::NLD; ++j) {
+          const int kk = j * 64 + 2 * lane;
+#pragma unroll
+          for (int c = 0; c < P; ++c) {
+            const double2 v = *reinterpret_cast<const double2*>(Vb + c * T::VSTR + kk);
+            acc[(2 * j) % T::NS][c] = fma(acur[j].x, v.x, acc[(2 * j) % T::NS][c]);
+            acc[(2 * j + 1) % T::NS][c] = fma(acur[j].y, v.y, acc[(2 * j + 1) % T::NS][c]);
+          }
+        }
+      }
+      if (more) store_v_chunk<P>(Vs + ((ch + 1) & 1) * (P * T::VSTR), vreg);
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < T::NLD; ++j) acur[j] = anxt[j];
+    }
+    double tot[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      double t = acc[0][c];
+#pragma unroll
+      for (int s = 1; s < T::NS; ++s) t += acc[s][c];
+      tot[c] = t;
+    }
+    ReduceScatter<P, 16>::run(tot, lane);
+    const int c = lane >> (5 - T::LOGP);
+    const bool owner = (lane & ((32 >> T::LOGP) - 1)) == 0;
+    if (valid && owner && c < pk) {
+      double y = tot[0];
+      if (sub_b) y -= prm.b[row];
+      Y[row * ldy + c] = y;
+    }
+  }
+  __syncthreads();
+}
+
+// Per-CTA partial Grams over the rows [r0, r1) of blocks with leading
+// dimension ld:  out[g0 + a*kMaxP + c] = sum_i U0[i,a] V0[i,c]  (U0 != NULL)
+//                out[g1 + a*kMaxP + c] = sum_i U1[i,a] V1[i,c]  (U1 != NULL)
+//                out[kSlotVec + a]    = sum_i S[i,a]^2          (S != NULL)
+// Each entry is one thread's compensated sum over i in row order (hi at
+// [slot], lo at [kPartHalf + slot]).
+__device__ void partial_grams(const double* U0, const double* V0, const double* U1,
+                              const double* V1, const double* S, int ld, int pk,
+                              int64_t r0, int64_t r1, double* out) {
+  const int sq = pk * pk;
+  const int total = 2 * sq + pk;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    const double* U;
+    const double* Vv;
+    int a, c, slot;
+    if (e < sq) {
+      U = U0; Vv = V0; a = e / pk; c = e - a * pk; slot = kSlotGram0 + a * kMaxP + c;
+    } else if (e < 2 * sq) {
+      const int f = e - sq;
+      U = U1; Vv = V1; a = f / pk; c = f - a * pk; slot = kSlotGram1 + a * kMaxP + c;
+    } else {
+      U = S; Vv = S; a = c = e - 2 * sq; slot = kSlotVec + a;
+    }
+    if (U == nullptr) continue;
+    DSum t{0.0, 0.0};
+    for (int64_t i = r0; i < r1; ++i) dsum_fma(t, ldcg(U + i * ld + a), ldcg(Vv + i * ld + c));
+    out[slot] = t.hi;
+    out[kPartHalf + slot] = t.lo;
+  }
+}
+
+// Per-CTA compensated sum of squares of x[i * ld] over the rows [r0, r1)
+// by warp 0, into `slot` (default: the scalar slot).
+__device__ void partial_sumsq(const double* x, int ld, int64_t r0, int64_t r1, double* out,
+                              int slot = kSlotScalar) {
+  if (threadIdx.x < 32) {
+    DSum t{0.0, 0.0};
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += 32) {
+      const double v = ldcg(x + i * ld);
+      dsum_fma(t, v, v);
+    }
+    t = dsum_warp(t);
+    if (threadIdx.x == 0) {
+      out[slot] = t.hi;
+      out[kPartHalf + slot] = t.lo;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Serial steps (run by the last-arriving CTA only).
+// --------------------------------------------------------------------------
+constexpr int kLd = kMaxP + 1;  // padded stride of the p x p smem matrices
+struct SerialSmem {
+  double m[kMaxP * kLd];
+  double g[kMaxP * kLd];
+  double l[kMaxP * kLd];
+  double y[kMaxP * kLd];
+  double sc[kMaxP];
+  double s2[kMaxP];
+  int keep[kMaxP];
+  int flag[4];
+};
+
+// Compensated sum of a slot entry over the CTAs, in CTA order.
+__device__ __forceinline__ double sum_parts(const Params& prm, int off) {
+  DSum t{0.0, 0.0};
+  const int G = gridDim.x;
+  for (int g = 0; g < G; ++g) {
+    const double* q = prm.part + (size_t)g * kPartStride;
+    dsum_add(t, ldcg(q + off), ldcg(q + kPartHalf + off));
+  }
+  return __dadd_rn(t.hi, t.lo);
+}
+
+// Y <- L^{-T} L^{-1} Y for m right-hand sides (thread per column), L lower.
+__device__ void chol_solve_cols(const double* l, double* y, int m) {
+  const int c = threadIdx.x;
+  if (c < m) {
+    for (int a = 0; a < m; ++a) {
+      double v = y[a * kLd + c];
+      for (int u = 0; u < a; ++u) v -= l[a * kLd + u] * y[u * kLd + c];
+      y[a * kLd + c] = v / l[a * kLd + a];
+    }
+    for (int a = m - 1; a >= 0; --a) {
+      double v = y[a * kLd + c];
+      for (int u = a + 1; u < m; ++u) v -= l[u * kLd + a] * y[u * kLd + c];
+      y[a * kLd + c] = v / l[a * kLd + a];
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// Stop test on the residual norms s2 (squared), shared by the init, beta and
+// replacement steps: sets s, jbest, relres_recur and the next ctrl.
+__device__ void stop_test(const Params& prm, SerialSmem& S, int pk, int where) {
+  DevState* st = prm.st;
+  if (threadIdx.x == 0) {
+    bool bad = false;
+    int jmin = 0;
+    for (int j = 0; j < pk; ++j) {
+      const double s = sqrt(S.s2[j]);
+      st->s[j] = s;
+      if (!finite(s)) bad = true;
+      if (j > 0 && s < sqrt(S.s2[jmin])) jmin = j;
+    }
+    if (bad) {
+      set_error(st, ST_ERR_NUMERICAL, where);
+    } else {
+      const double smin = sqrt(S.s2[jmin]);
+      const double bn = ldcg(&st->bnorm);
+      const bool stop = smin <= prm.tol * bn;
+      st->jbest = jmin;
+      st->relres_recur = smin / bn;
+      const bool done = stop || ldcg(&st->k) >= prm.maxit;
+      if (done && prm.skip_true_check) {
+        // inner solve: the recurrence residual decides (the caller checks the
+        // true residual of its own, outer system)
+        st->relres_true = smin / bn;
+        st->result = stop ? ST_OK : ST_NOT_CONVERGED;
+        st->ctrl = CTRL_FINISH;
+      } else {
+        st->ctrl = done ? CTRL_CHECK : CTRL_LOOP;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// alpha step: M, G -> rank test, factor, alpha_k^T (Algorithm 2 / 3).
+__device__ void serial_alpha(const Params& prm, SerialSmem& S) {
+  DevState* st = prm.st;
+  const int tid = threadIdx.x;
+  const int pk = ldcg(&st->pk);
+  const int sq = pk * pk;
+  if (tid < 4) S.flag[tid] = 0;
+  for (int e = tid; e < 2 * sq; e += kThreads) {
+    const int f = e < sq ? e : e - sq;
+    const int a = f / pk, c = f - a * pk;
+    const int off = (e < sq ? kSlotGram0 : kSlotGram1) + a * kMaxP + c;
+    (e < sq ? S.m : S.g)[a * kLd + c] = sum_parts(prm, off);
+  }
+  __syncthreads();
+  // M <- (M + M^T) / 2
+  for (int e = tid; e < sq; e += kThreads) {
+    const int a = e / pk, c = e - a * pk;
+    if (c < a) {
+      const double v = 0.5 * (S.m[a * kLd + c] + S.m[c * kLd + a]);
+      S.m[a * kLd + c] = v;
+      S.m[c * kLd + a] = v;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < sq; e += kThreads) {
+    const int a = e / pk, c = e - a * pk;
+    if (!finite(S.m[a * kLd + c]) || !finite(S.g[a * kLd + c])) S.flag[0] = 1;
+  }
+  if (tid < pk) {
+    const double mjj = S.m[tid * kLd + tid];
+    if (mjj < 0.0) S.flag[1] = 1;
+    S.sc[tid] = mjj > 0.0 ? 1.0 / sqrt(mjj) : 0.0;
+  }
+  __syncthreads();
+  if (S.flag[0] || S.flag[1]) {
+    if (tid == 0) set_error(st, S.flag[0] ? ST_ERR_NUMERICAL : ST_ERR_NOT_SPD, 1);
+    __syncthreads();
+    return;
+  }
+  // scaled lower triangle, unit diagonal
+  for (int e = tid; e < sq; e += kThreads) {
+    const int a = e / pk, c = e - a * pk;
+    if (c < a) S.l[a * kLd + c] = (S.sc[a] * S.m[a * kLd + c]) * S.sc[c];
+    else if (c == a) S.l[a * kLd + a] = 1.0;
+  }
+  __syncthreads();
+  // right-looking Cholesky, columns in agent order; a column whose pivot is
+  // below rank_tol is skipped (agent dropped, Algorithm 3)
+  const double neg_lim = -sqrt(prm.rank_tol);
+  int m = 0;
+  for (int j = 0; j < pk; ++j) {
+    const double d = S.l[j * kLd + j];
+    const bool zero_dir = S.m[j * kLd + j] == 0.0;
+    int decision = 0;  // 0 keep, 1 drop, 2 not SPD, 3 NaN
+    if (zero_dir) decision = 1;
+    else if (!(d == d)) decision = 3;
+    else if (d < neg_lim) decision = 2;
+    else if (d < prm.rank_tol) decision = 1;
+    if (decision >= 2) {
+      if (tid == 0) set_error(st, decision == 2 ? ST_ERR_NOT_SPD : ST_ERR_NUMERICAL, 2);
+      __syncthreads();
+      return;
+    }
+    if (decision == 1) continue;
+    const double ljj = sqrt(d);
+    __syncthreads();
+    if (tid == 0) { S.l[j * kLd + j] = ljj; S.keep[m] = j; }
+    for (int i = j + 1 + tid; i < pk; i += kThreads) S.l[i * kLd + j] /= ljj;
+    __syncthreads();
+    const int nt = pk - j - 1;
+    for (int e = tid; e < nt * nt; e += kThreads) {
+      const int ii = j + 1 + e / nt, ll = j + 1 + e % nt;
+      if (ll <= ii) S.l[ii * kLd + ll] -= S.l[ii * kLd + j] * S.l[ll * kLd + j];
+    }
+    ++m;
+    __syncthreads();
+  }
+  if (m == 0) {
+    if (tid == 0) set_error(st, ST_ERR_NUMERICAL, 3);
+    __syncthreads();
+    return;
+  }
+  // restricted factor -> y (as scratch) then st->L; restricted sc
+  for (int e = tid; e < m * m; e += kThreads) {
+    const int a = e / m, c = e - a * m;
+    const double v = (c <= a) ? S.l[S.keep[a] * kLd + S.keep[c]] : 0.0;
+    S.y[a * kLd + c] = v;
+    st->L[a * kMaxP + c] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += kThreads) {
+    const int a = e / m, c = e - a * m;
+    S.m[a * kLd + c] = S.y[a * kLd + c];  // factor
+    // right-hand sides: Y[a][c] = sc[a] * G[c][a] on the kept set
+    S.l[a * kLd + c] = S.sc[S.keep[a]] * S.g[S.keep[c] * kLd + S.keep[a]];
+  }
+  __syncthreads();
+  chol_solve_cols(S.m, S.l, m);
+  for (int e = tid; e < m * m; e += kThreads) {
+    const int b = e / m, a = e - b * m;
+    const double v = -S.sc[S.keep[b]] * S.l[b * kLd + a];
+    st->alphaT[b * kMaxP + a] = v;
+    if (!finite(v)) S.flag[2] = 1;
+  }
+  if (tid < m) st->sc[tid] = S.sc[S.keep[tid]];
+  __syncthreads();
+  if (S.flag[2]) {
+    if (tid == 0) set_error(st, ST_ERR_NUMERICAL, 4);
+    __syncthreads();
+    return;
+  }
+  if (tid == 0) {
+    st->prev_pk = pk;
+    st->changed = (m < pk) ? 1 : 0;
+    if (m < pk) {
+      int old[kMaxP];
+      for (int j = 0; j < pk; ++j) {
+        old[j] = ldcg(&st->agent[j]);
+        st->old_agent[j] = old[j];
+      }
+      for (int j = 0; j < m; ++j) {
+        st->keep[j] = S.keep[j];
+        st->agent[j] = old[S.keep[j]];
+      }
+      st->drops = ldcg(&st->drops) + (pk - m);
+      st->pk = m;
+    }
+  }
+  __syncthreads();
+}
+
+// beta step: H, s2 -> beta_k^T, iteration count, stop test.
+__device__ void serial_beta(const Params& prm, SerialSmem& S) {
+  DevState* st = prm.st;
+  const int tid = threadIdx.x;
+  const int pk = ldcg(&st->pk);
+  const int sq = pk * pk;
+  if (tid < 4) S.flag[tid] = 0;
+  for (int e = tid; e < sq + pk; e += kThreads) {
+    if (e < sq) {
+      const int a = e / pk, c = e - a * pk;
+      S.g[a * kLd + c] = sum_parts(prm, kSlotGram0 + a * kMaxP + c);
+    } else {
+      S.s2[e - sq] = sum_parts(prm, kSlotVec + (e - sq));
+    }
+  }
+  for (int e = tid; e < sq; e += kThreads) {
+    const int a = e / pk, c = e - a * pk;
+    S.m[a * kLd + c] = ldcg(&st->L[a * kMaxP + c]);
+  }
+  if (tid < pk) S.sc[tid] = ldcg(&st->sc[tid]);
+  __syncthreads();
+  for (int e = tid; e < sq; e += kThreads) {
+    const int a = e / pk, c = e - a * pk;
+    if (!finite(S.g[a * kLd + c])) S.flag[0] = 1;
+    S.l[a * kLd + c] = S.sc[a] * S.g[c * kLd + a];
+  }
+  __syncthreads();
+  if (S.flag[0]) {
+    if (tid == 0) set_error(st, ST_ERR_NUMERICAL, 5);
+    __syncthreads();
+    return;
+  }
+  chol_solve_cols(S.m, S.l, pk);
+  for (int e = tid; e < sq; e += kThreads) {
+    const int b = e / pk, a = e - b * pk;
+    const double v = -S.sc[b] * S.l[b * kLd + a];
+    st->betaT[b * kMaxP + a] = v;
+    if (!finite(v)) S.flag[1] = 1;
+  }
+  if (tid == 0) st->k = ldcg(&st->k) + 1;
+  __syncthreads();
+  if (S.flag[1]) {
+    if (tid == 0) set_error(st, ST_ERR_NUMERICAL, 6);
+    __syncthreads();
+    return;
+  }
+  stop_test(prm, S, pk, 7);
+}
+
+__device__ void serial_bnorm(const Params& prm, SerialSmem& S) {
+  DevState* st = prm.st;
+  if (threadIdx.x == 0) {
+    const double b2 = sum_parts(prm, kSlotScalar);
+    const double bn = sqrt(b2);
+    st->bnorm = bn;
+    if (!finite(bn)) {
+      set_error(st, ST_ERR_NUMERICAL, 8);
+    } else if (bn == 0.0) {
+      st->zero_rhs = 1;
+      st->jbest = 0;
+      st->result = ST_OK;
+      st->ctrl = CTRL_FINISH;
+    } else {
+      st->ctrl = CTRL_LOOP;
+    }
+  }
+  __syncthreads();
+}
+
+// init / replacement: residual norms of R = A X - b 1^T.
+__device__ void serial_norms(const Params& prm, SerialSmem& S, bool replacement) {
+  DevState* st = prm.st;
+  const int pk = ldcg(&st->pk);
+  for (int e = threadIdx.x; e < pk; e += kThreads) S.s2[e] = sum_parts(prm, kSlotVec + e);
+  if (threadIdx.x == 0 && replacement) {
+    st->replacements = ldcg(&st->replacements) + 1;
+    st->k_replaced = ldcg(&st->k);
+  }
+  __syncthreads();
+  stop_test(prm, S, pk, replacement ? 9 : 10);
+}
+
+__device__ void serial_check(const Params& prm) {
+  DevState* st = prm.st;
+  if (threadIdx.x == 0) {
+    const double tr = sqrt(sum_parts(prm, kSlotScalar)) / ldcg(&st->bnorm);
+    st->relres_true = tr;
+    if (!finite(tr)) {
+      set_error(st, ST_ERR_NUMERICAL, 11);
+    } else if (tr <= prm.tol) {
+      st->result = ST_OK;
+      st->ctrl = CTRL_FINISH;
+    } else if (ldcg(&st->k) >= prm.maxit || !prm.replacement ||
+               ldcg(&st->k) == ldcg(&st->k_replaced)) {
+      st->result = ST_NOT_CONVERGED;
+      st->ctrl = CTRL_FINISH;
+    } else {
+      st->ctrl = CTRL_REPLACE;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void serial_block_product(const Params& prm, SerialSmem& S) {
+  DevState* st = prm.st;
+  const int q = prm.q;
+  const int sq = q * q;
+  for (int e = threadIdx.x; e < 2 * sq; e += kThreads) {
+    const int f = e < sq ? e : e - sq;
+    const int a = f / q, c = f - a * q;
+    const int off = (e < sq ? kSlotGram0 : kSlotGram1) + a * kMaxP + c;
+    (e < sq ? S.m : S.g)[a * kLd + c] = sum_parts(prm, off);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < sq; e += kThreads) {
+    const int a = e / q, c = e - a * q;
+    double v = S.m[a * kLd + c];
+    if (c != a) v = 0.5 * (S.m[a * kLd + c] + S.m[c * kLd + a]);
+    st->gram_out[a * kMaxP + c] = v;
+    st->gram_out[kSq + a * kMaxP + c] = S.g[a * kLd + c];
+  }
+  if (threadIdx.x == 0) st->result = ST_OK;
+  __syncthreads();
+}
+
+
+// FP8 operand: column scales sigma_j = max_i |V_ij| / 448 from the per-CTA
+// maxima in the vector slot (hi part).
+__device__ void serial_sigma(const Params& prm, int pk) {
+  DevState* st = prm.st;
+  if (threadIdx.x < pk) {
+    float m = 0.f;
+    const int G = gridDim.x;
+    for (int g = 0; g < G; ++g)
+      m = fmaxf(m, (float)ldcg(prm.part + (size_t)g * kPartStride + kSlotVec + threadIdx.x));
+    st->sigma[threadIdx.x] = m > 0.f ? m / 448.f : 1.f;
+    if (!(m == m) || isinf(m)) set_error(st, ST_ERR_NUMERICAL, 12);
+  }
+  __syncthreads();
+}
+
+// Refinement step: ||b|| (vector slot 0) and ||A x - b|| (scalar slot).
+__device__ void serial_refine(const Params& prm) {
+  DevState* st = prm.st;
+  if (threadIdx.x == 0) {
+    const double bn = sqrt(sum_parts(prm, kSlotVec));
+    const double rn = sqrt(sum_parts(prm, kSlotScalar));
+    st->bnorm = bn;
+    st->rnorm = rn;
+    st->relres_true = bn > 0.0 ? rn / bn : rn;
+    if (!finite(rn) || !finite(bn)) set_error(st, ST_ERR_NUMERICAL, 13);
+  }
+  __syncthreads();
+}
+
+
+// --------------------------------------------------------------------------
+// Tensor-core A-pass of the inner low-precision solves (policy != POL_FP64).
+// The quantised A (BF16, or FP8 E4M3 with row scales) streams through a TMA
+// ring into tcgen05.mma; the operand block is converted to the MMA type by
+// the rows' owners first.  Work is split stream-K over (row tile, k-chunk)
+// units exactly as in the standalone block product; after a grid barrier the
+// owner of each row sums the partial tiles that cover it, in CTA order, and
+// applies the scales.  The ring position, phases and accumulator-buffer
+// counts live in shared memory, so every A-pass resumes where the previous
+// one stopped.
+// --------------------------------------------------------------------------
+struct LpShared {
+  int p_stage;
+  unsigned p_phase;
+  int m_stage;
+  unsigned m_phase;
+  int m_seg;
+  int m_any;
+  int e_seg[4];             // per epilogue warp
+  unsigned tmem;
+  int issued[tc::kStages];  // phase of the last copy issued on each stage, -1 = none
+};
+
+template <int POL>
+struct LpCfg {
+  static constexpr int KIND = (POL == POL_FP8) ? tc::KIND_FP8 : tc::KIND_BF16;
+};
+
+template <int P>
+struct LpNP {
+  static constexpr int value = (P <= 16) ? 16 : 32;
+};
+
+template <int KIND, int NP>
+struct LpLayout {
+  using S = tc::Shape<KIND, NP>;
+  static constexpr int kBars = 2 * tc::kStages + 5;  // full, empty, accf[2], acce[2], drain
+  static constexpr size_t kBytes = 1024 + S::kRingBytes + kBars * 8 + sizeof(LpShared) + 64;
+};
+
+struct LpCtx {
+  uint8_t* ring;
+  uint64_t* bars;
+  LpShared* sh;
+};
+
+// Wait without regard to the error flag (teardown drains), bounded.
+__device__ void mbar_wait_drain(uint32_t a, uint32_t parity, long long timeout_ns) {
+  const unsigned long long t0 = globaltimer_ns();
+  while (!tc::mbar_try(a, parity)) {
+    if (globaltimer_ns() - t0 > (unsigned long long)timeout_ns) return;
+    __nanosleep(64);
+  }
+}
+
+template <int KIND, int NP>
+__device__ void lp_pass(const Params& prm, LpCtx& L) {
+  using S = tc::Shape<KIND, NP>;
+  constexpr uint32_t kIdesc = tc::idesc<KIND>(NP);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  const int c = blockIdx.x;
+  const int64_t U = prm.lp_units;
+  const int kc = prm.lp_kc;
+  const int64_t u0 = tc::unit_begin(U, G, c);
+  const int64_t u1 = tc::unit_begin(U, G, c + 1);
+  uint8_t* sA = L.ring;
+  uint8_t* sB = L.ring + tc::kStages * tc::kTileABytes;
+  uint64_t* full = L.bars;
+  uint64_t* empty = L.bars + tc::kStages;
+  uint64_t* accf = L.bars + 2 * tc::kStages;
+  uint64_t* acce = accf + 2;
+  int* err = &prm.st->error;
+  const long long to = prm.timeout_ns;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // operand rows were written through the generic proxy before the barrier
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      int stage = L.sh->p_stage;
+      uint32_t phase = L.sh->p_phase;
+      for (int64_t u = u0; u < u1; ++u) {
+        if (!tc::mbar_wait(tc::smem_u32(&empty[stage]), phase ^ 1u, to, err)) break;
+        const int t = (int)(u / kc);
+        const int k = (int)(u % kc);
+        const uint32_t fb = tc::smem_u32(&full[stage]);
+        tc::mbar_expect_tx(fb, S::kStageBytes);
+        tc::tma_load_2d(tc::smem_u32(sA + stage * tc::kTileABytes), &prm.lp_tmA,
+                        k * prm.lp_kelems, t * tc::kBM, fb);
+        tc::tma_load_2d(tc::smem_u32(sB + stage * S::kTileBBytes), &prm.lp_tmB,
+                        k * prm.lp_kelems, 0, fb);
+        L.sh->issued[stage] = (int)phase;
+        if (++stage == tc::kStages) { stage = 0; phase ^= 1u; }
+      }
+      L.sh->p_stage = stage;
+      L.sh->p_phase = phase;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = L.sh->m_stage;
+      uint32_t phase = L.sh->m_phase;
+      int seg = L.sh->m_seg;
+      const uint32_t tmem = L.sh->tmem;
+      for (int64_t u = u0; u < u1; ++u) {
+        const int k = (int)(u % kc);
+        const bool first = (u == u0) || (k == 0);
+        const bool last = (u == u1 - 1) || (k == kc - 1);
+        const int b = seg & 1;
+        if (first) {
+          if (!tc::mbar_wait(tc::smem_u32(&acce[b]), (((uint32_t)seg >> 1) & 1u) ^ 1u, to, err)) break;
+          tc::fence_after();
+        }
+        if (!tc::mbar_wait(tc::smem_u32(&full[stage]), phase, to, err)) break;
+        tc::fence_after();
+        const uint32_t dt = tmem + (uint32_t)(b * NP);
+        const uint64_t ad = tc::sdesc(tc::smem_u32(sA + stage * tc::kTileABytes));
+        const uint64_t bd = tc::sdesc(tc::smem_u32(sB + stage * S::kTileBBytes));
+#pragma unroll
+        for (int kk = 0; kk < tc::kRowBytes / 32; ++kk) {
+          tc::mma<KIND>(dt, ad + 2u * kk, bd + 2u * kk, kIdesc, (first && kk == 0) ? 0u : 1u);
+          if constexpr (KIND == tc::KIND_FP8) {
+            const uint64_t bl = tc::sdesc(tc::smem_u32(sB + stage * S::kTileBBytes + NP * tc::kRowBytes));
+            tc::mma<KIND>(dt, ad + 2u * kk, bl + 2u * kk, kIdesc, 1u);
+          }
+        }
+        L.sh->m_any = 1;
+        tc::mma_commit(tc::smem_u32(&empty[stage]));
+        if (last) {
+          tc::mma_commit(tc::smem_u32(&accf[b]));
+          ++seg;
+        }
+        if (++stage == tc::kStages) { stage = 0; phase ^= 1u; }
+      }
+      L.sh->m_stage = stage;
+      L.sh->m_phase = phase;
+      L.sh->m_seg = seg;
+    }
+  } else if (warp >= 4) {
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    int seg = L.sh->e_seg[quad];
+    if (u0 < u1) {
+      const int t0 = (int)(u0 / kc);
+      const int t1 = (int)((u1 - 1) / kc);
+      for (int t = t0; t <= t1; ++t, ++seg) {
+        const int b = seg & 1;
+        if (!tc::mbar_wait(tc::smem_u32(&accf[b]), ((uint32_t)seg >> 1) & 1u, to, err)) break;
+        tc::fence_after();
+        float v[NP];
+        tc::tmem_ld<NP>(L.sh->tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * NP), v);
+        float* dst = prm.lp_part + ((size_t)(c + t) * tc::kBM + row) * NP;
+#pragma unroll
+        for (int j = 0; j < NP; j += 4)
+          *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(tc::smem_u32(&acce[b]));
+      }
+    }
+    __syncwarp();
+    if (lane == 0) L.sh->e_seg[quad] = seg;
+  }
+  __syncthreads();
+}
+
+// Y[:, 0:pk] = A_lp V[:, 0:pk] (- b) on the rows [r0, r1) of this CTA, with the
+// operand conversion, the tensor-core pass and the fixup.  false = leave.
+template <int P, int POL>
+__device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, bool sub_b,
+                         int64_t r0, int64_t r1, LpCtx& L, SyncShared* ss, int* s_err) {
+  constexpr int KIND = LpCfg<POL>::KIND;
+  constexpr int NP = LpNP<P>::value;
+  DevState* st = prm.st;
+  const int p = prm.p;
+  const int tid = threadIdx.x;
+  const int64_t nr = r1 - r0;
+  const int64_t ldk = prm.lp_ldk;
+  double* mypart = prm.part + (size_t)blockIdx.x * kPartStride;
+
+  if constexpr (KIND == tc::KIND_FP8) {
+    for (int j = tid; j < pk; j += kThreads) {
+      float m = 0.f;
+      for (int64_t i = r0; i < r1; ++i) m = fmaxf(m, (float)fabs(ldcg(V + i * p + j)));
+      mypart[kSlotVec + j] = (double)m;
+    }
+    const int f = grid_arrive(prm, ss);
+    if (f < 0) return false;
+    if (f == 1) {
+      if (!cta_error(st, s_err)) serial_sigma(prm, pk);
+      grid_release(prm, ss);
+    }
+    if (cta_error(st, s_err)) return false;
+  }
+  // operand row j (< NP) holds column j of V, zero beyond pk
+  for (int64_t idx = tid; idx < (int64_t)NP * nr; idx += kThreads) {
+    const int j = (int)(idx / nr);
+    const int64_t i = r0 + (idx - (int64_t)j * nr);
+    const double v = (j < pk) ? ldcg(V + i * p + j) : 0.0;
+    if constexpr (KIND == tc::KIND_BF16) {
+      reinterpret_cast<__nv_bfloat16*>(prm.lp_dq)[(int64_t)j * ldk + i] = __double2bfloat16(v);
+    } else {
+      const float sg = (j < pk) ? __ldcg(&st->sigma[j]) : 1.f;
+      const double x = v / (double)sg;
+      const __nv_fp8_storage_t h = __nv_cvt_double_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+      const double hv = (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(h, __NV_E4M3)));
+      const __nv_fp8_storage_t l = __nv_cvt_double_to_fp8(x - hv, __NV_SATFINITE, __NV_E4M3);
+      uint8_t* o = reinterpret_cast<uint8_t*>(prm.lp_dq);
+      o[(int64_t)j * ldk + i] = (uint8_t)h;
+      o[(int64_t)(NP + j) * ldk + i] = (uint8_t)l;
+    }
+  }
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  if (!grid_barrier(prm, ss, s_err)) return false;
+  lp_pass<KIND, NP>(prm, L);
+  if (!grid_barrier(prm, ss, s_err)) return false;
+  // fixup: each owned row sums the partial tiles of the CTAs that covered it
+  const int G = gridDim.x;
+  const int64_t U = prm.lp_units;
+  const int kc = prm.lp_kc;
+  for (int64_t idx = tid; idx < nr * pk; idx += kThreads) {
+    const int64_t i = r0 + idx / pk;
+    const int j = (int)(idx - (idx / pk) * pk);
+    const int t = (int)(i / tc::kBM);
+    const int rr = (int)(i - (int64_t)t * tc::kBM);
+    const int64_t lo = (int64_t)t * kc, hi = lo + kc;
+    int c0 = (int)((lo * G) / U);
+    while (c0 > 0 && tc::unit_begin(U, G, c0) > lo) --c0;
+    while (tc::unit_begin(U, G, c0 + 1) <= lo) ++c0;
+    double s = 0.0;
+    for (int cc = c0; cc < G && tc::unit_begin(U, G, cc) < hi; ++cc) {
+      if (tc::unit_begin(U, G, cc + 1) <= tc::unit_begin(U, G, cc)) continue;
+      s += (double)__ldcg(prm.lp_part + ((size_t)(cc + t) * tc::kBM + rr) * NP + j);
+    }
+    if (prm.lp_row_scale) s *= (double)prm.lp_row_scale[i];
+    if constexpr (KIND == tc::KIND_FP8) s *= (double)__ldcg(&st->sigma[j]);
+    if (sub_b) s -= prm.b[i];
+    Y[i * p + j] = s;
+  }
+  __syncthreads();
+  return true;
+}
+
+// --------------------------------------------------------------------------
+// The persistent kernel.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double splitmix_uniform(unsigned long long seed,
+                                                   unsigned long long c) {
+  // SplitMix64 output number c+1 of the stream seeded with `seed`
+  // (Steele, Lea, Flood 2014); top 53 bits -> [0, 1).
+  unsigned long long z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+template <int P, bool VEC, int POL>
+__device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCtx* L) {
+  __shared__ SyncShared ss;
+  __shared__ int s_int[4];
+  __shared__ int s_err;
+  SerialSmem& S = *reinterpret_cast<SerialSmem*>(smem);
+  DevState* st = prm.st;
+  const int G = gridDim.x;
+  const int cta = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int64_t n = prm.n;
+  const int64_t r0 = ((int64_t)cta * n) / G;
+  const int64_t r1 = ((int64_t)(cta + 1) * n) / G;
+  const int p = prm.p;
+  double* mypart = prm.part + (size_t)cta * kPartStride;
+
+#define CCG_SYNC_SERIAL(CALL)              \
+  {                                        \
+    const int f_ = grid_arrive(prm, &ss);  \
+    if (f_ < 0) return;                    \
+    if (f_ == 1) {                         \
+      if (!cta_error(st, &s_err)) {        \
+        CALL;                              \
+      }                                    \
+      grid_release(prm, &ss);              \
+    }                                      \
+    if (cta_error(st, &s_err)) return;     \
+  }
+
+  if (prm.mode == MODE_BARRIER_SELFTEST) {
+    grid_barrier(prm, &ss, &s_err);
+    return;
+  }
+
+  if constexpr (POL == POL_FP64) {
+    if (prm.mode == MODE_BLOCK_PRODUCT) {
+      const int q = prm.q;
+      apass<P, VEC>(prm, prm.V, q, 0, q, prm.Wout, q, false, r0, r1, smem);
+      partial_grams(prm.V, prm.Wout, prm.U, prm.U ? prm.V : nullptr, nullptr, q, q, r0, r1,
+                    mypart);
+      CCG_SYNC_SERIAL(serial_block_product(prm, S));
+      return;
+    }
+    if (prm.mode == MODE_REFINE) {
+      // x += c delta ; r = A x - b (FP64) ; ||b||, ||r|| ; b_in = -r sqrt(n) / ||r||
+      if (prm.ref_delta != nullptr)
+        for (int64_t i = r0 + tid; i < r1; i += kThreads)
+          prm.ref_x[i] = fma(prm.ref_coef, prm.ref_delta[i], prm.ref_x[i]);
+      if (!grid_barrier(prm, &ss, &s_err)) return;
+      apass<1, VEC>(prm, prm.ref_x, 1, 0, 1, prm.ref_r, 1, true, r0, r1, smem);
+      partial_sumsq(prm.ref_r, 1, r0, r1, mypart, kSlotScalar);
+      __syncthreads();
+      partial_sumsq(prm.b, 1, r0, r1, mypart, kSlotVec);
+      CCG_SYNC_SERIAL(serial_refine(prm));
+      const double rn = ldcg(&st->rnorm);
+      const double scale = rn > 0.0 ? sqrt((double)n) / rn : 0.0;
+      for (int64_t i = r0 + tid; i < r1; i += kThreads) prm.ref_bin[i] = -ldcg(prm.ref_r + i) * scale;
+      return;
+    }
+  } else {
+    if (prm.mode != MODE_SOLVE || !prm.skip_true_check) {
+      if (tid == 0 && cta == 0) set_error(st, ST_ERR_INVALID, 14);
+      return;
+    }
+  }
+
+  // ---- initial block X_0 and ||b|| ----
+  for (int64_t idx = r0 * p + tid; idx < r1 * p; idx += kThreads) {
+    const int64_t i = idx / p;
+    const int j = (int)(idx - i * p);
+    double v;
+    if (prm.X0 != nullptr) {
+      v = prm.X0[idx];
+    } else {
+      const double base = prm.x0 ? prm.x0[i] : 0.0;
+      if (j == 0) {
+        v = base;
+      } else {
+        const double u = splitmix_uniform(prm.seed, (unsigned long long)j * (unsigned long long)n +
+                                                        (unsigned long long)i);
+        v = __dadd_rn(base, __dmul_rn(prm.spread, __dsub_rn(2.0 * u, 1.0)));
+      }
+    }
+    prm.X[idx] = v;
+  }
+  partial_sumsq(prm.b, 1, r0, r1, mypart);
+  CCG_SYNC_SERIAL(serial_bnorm(prm, S));
+
+  if (tid == 0) s_int[0] = ldcg(&st->ctrl);
+  __syncthreads();
+  if (s_int[0] != CTRL_FINISH) {
+    // R_0 = A X_0 - b 1^T ; D_0 = R_0
+    if constexpr (POL == POL_FP64) {
+      apass<P, VEC>(prm, prm.X, p, 0, p, prm.R, p, true, r0, r1, smem);
+    } else {
+      if (!lp_apass<P, POL>(prm, prm.X, p, prm.R, true, r0, r1, *L, &ss, &s_err)) return;
+    }
+    for (int64_t idx = r0 * p + tid; idx < r1 * p; idx += kThreads) prm.D0[idx] = ldcg(prm.R + idx);
+    partial_grams(nullptr, nullptr, nullptr, nullptr, prm.R, p, p, r0, r1, mypart);
+    CCG_SYNC_SERIAL(serial_norms(prm, S, false));
+  }
+
+  int cur = 0;
+  for (;;) {
+    if (tid == 0) {
+      s_int[0] = ldcg(&st->ctrl);
+      s_int[1] = ldcg(&st->pk);
+    }
+    __syncthreads();
+    const int ctrl = s_int[0];
+    int pk = s_int[1];
+    double* D = cur ? prm.D1 : prm.D0;
+    double* Dn = cur ? prm.D0 : prm.D1;
+
+    if (ctrl == CTRL_FINISH) {
+      const int zero = ldcg(&st->zero_rhs);
+      const int jb = ldcg(&st->jbest);
+      for (int64_t i = r0 + tid; i < r1; i += kThreads)
+        prm.x_out[i] = zero ? 0.0 : ldcg(prm.X + i * p + jb);
+      if (prm.X_out != nullptr) {
+        for (int64_t idx = r0 * p + tid; idx < r1 * p; idx += kThreads) {
+          const int64_t i = idx / p;
+          const int c = (int)(idx - i * p);
+          if (zero) prm.X_out[idx] = 0.0;
+          else if (c < pk) prm.X_out[i * p + ldcg(&st->agent[c])] = ldcg(prm.X + idx);
+        }
+      }
+      return;
+    }
+
+    if constexpr (POL != POL_FP64) {
+      if (ctrl == CTRL_CHECK || ctrl == CTRL_REPLACE) {  // never reached by inner solves
+        if (tid == 0) set_error(st, ST_ERR_INVALID, 15);
+        return;
+      }
+    }
+
+    if (ctrl == CTRL_CHECK) {
+      // true residual of the best agent: W[:, 0] = A X e_jb - b
+      const int jb = ldcg(&st->jbest);
+      if constexpr (POL == POL_FP64) {
+        apass<1, VEC>(prm, prm.X, p, jb, 1, prm.W, p, true, r0, r1, smem);
+        partial_sumsq(prm.W, p, r0, r1, mypart);
+        CCG_SYNC_SERIAL(serial_check(prm));
+      }
+      continue;
+    }
+
+    if (ctrl == CTRL_REPLACE) {
+      if constexpr (POL == POL_FP64) apass<P, VEC>(prm, prm.X, p, 0, pk, prm.R, p, true, r0, r1, smem);
+      for (int64_t idx = r0 * p + tid; idx < r1 * p; idx += kThreads) {
+        const int c = (int)(idx % p);
+        if (c < pk) D[idx] = ldcg(prm.R + idx);
+      }
+      partial_grams(nullptr, nullptr, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
+      CCG_SYNC_SERIAL(serial_norms(prm, S, true));
+      continue;
+    }
+
+    // ---- one cCG iteration ----
+    if constexpr (POL == POL_FP64) {
+      apass<P, VEC>(prm, D, p, 0, pk, prm.W, p, false, r0, r1, smem);
+    } else {
+      if (!lp_apass<P, POL>(prm, D, pk, prm.W, false, r0, r1, *L, &ss, &s_err)) return;
+    }
+    partial_grams(D, prm.W, prm.R, D, nullptr, p, pk, r0, r1, mypart);
+    CCG_SYNC_SERIAL(serial_alpha(prm, S));
+
+    if (tid == 0) {
+      s_int[2] = ldcg(&st->changed);
+      s_int[1] = ldcg(&st->pk);
+      s_int[3] = ldcg(&st->prev_pk);
+    }
+    __syncthreads();
+    if (s_int[2]) {
+      // restrict X, R, D, W to the kept agents (own rows, in place)
+      const int m = s_int[1];
+      const int ppk = s_int[3];
+      int* keep = reinterpret_cast<int*>(smem);
+      int* oldag = keep + kMaxP;
+      if (tid < ppk) {
+        keep[tid] = tid < m ? ldcg(&st->keep[tid]) : 0;
+        oldag[tid] = ldcg(&st->old_agent[tid]);
+      }
+      __syncthreads();
+      for (int64_t i = r0 + tid; i < r1; i += kThreads) {
+        double* rows[4] = {prm.X + i * p, prm.R + i * p, D + i * p, prm.W + i * p};
+        if (prm.X_out != nullptr) {
+          int t = 0;
+          for (int c = 0; c < ppk; ++c) {
+            if (t < m && keep[t] == c) { ++t; continue; }
+            prm.X_out[i * p + oldag[c]] = rows[0][c];
+          }
+        }
+        for (int r = 0; r < 4; ++r)
+          for (int c = 0; c < m; ++c) rows[r][c] = rows[r][keep[c]];
+      }
+      __syncthreads();
+    }
+    pk = s_int[1];
+
+    // X += D alpha^T ; R += W alpha^T
+    {
+      double* Ts = smem;
+      for (int e = tid; e < pk * pk; e += kThreads) {
+        const int b = e / pk, a = e - b * pk;
+        Ts[b * kLd + a] = ldcg(&st->alphaT[b * kMaxP + a]);
+      }
+      __syncthreads();
+      const int64_t cnt = (r1 - r0) * pk;
+      for (int64_t idx = tid; idx < cnt; idx += kThreads) {
+        const int64_t i = r0 + idx / pk;
+        const int a = (int)(idx % pk);
+        double dx = 0.0, dr = 0.0;
+        for (int b = 0; b < pk; ++b) {
+          const double t = Ts[b * kLd + a];
+          dx = fma(ldcg(D + i * p + b), t, dx);
+          dr = fma(ldcg(prm.W + i * p + b), t, dr);
+        }
+        prm.X[i * p + a] += dx;
+        prm.R[i * p + a] += dr;
+      }
+      __syncthreads();
+    }
+    partial_grams(prm.R, prm.W, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
+    CCG_SYNC_SERIAL(serial_beta(prm, S));
+
+    if (tid == 0) s_int[0] = ldcg(&st->ctrl);
+    __syncthreads();
+    if (s_int[0] == CTRL_LOOP) {
+      // D_{k+1} = R_{k+1} + D_k beta^T
+      double* Ts = smem;
+      for (int e = tid; e < pk * pk; e += kThreads) {
+        const int b = e / pk, a = e - b * pk;
+        Ts[b * kLd + a] = ldcg(&st->betaT[b * kMaxP + a]);
+      }
+      __syncthreads();
+      const int64_t cnt = (r1 - r0) * pk;
+      for (int64_t idx = tid; idx < cnt; idx += kThreads) {
+        const int64_t i = r0 + idx / pk;
+        const int a = (int)(idx % pk);
+        double acc = 0.0;
+        for (int b = 0; b < pk; ++b) acc = fma(ldcg(D + i * p + b), Ts[b * kLd + a], acc);
+        Dn[i * p + a] = ldcg(prm.R + i * p + a) + acc;
+      }
+      if (!grid_barrier(prm, &ss, &s_err)) return;
+      cur ^= 1;
+    }
+  }
+#undef CCG_SYNC_SERIAL
+}
+
+
+template <int P, bool VEC, int POL>
+__global__ void __launch_bounds__(kThreads, 1) fp64_kernel(const __grid_constant__ Params prm) {
+  extern __shared__ __align__(1024) uint8_t dyn_smem[];
+  if constexpr (POL == POL_FP64) {
+    solve_body<P, VEC, POL>(prm, reinterpret_cast<double*>(dyn_smem), nullptr);
+  } else {
+    constexpr int KIND = LpCfg<POL>::KIND;
+    constexpr int NP = LpNP<P>::value;
+    using Lay = LpLayout<KIND, NP>;
+    using S = tc::Shape<KIND, NP>;
+    uint8_t* base = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023));
+    LpCtx L;
+    L.ring = base;
+    L.bars = reinterpret_cast<uint64_t*>(base + S::kRingBytes);
+    L.sh = reinterpret_cast<LpShared*>(L.bars + Lay::kBars);
+    double* uni = reinterpret_cast<double*>(
+        (reinterpret_cast<uintptr_t>(L.sh + 1) + 15) & ~uintptr_t(15));
+    const int warp = threadIdx.x >> 5;
+    uint64_t* drain = L.bars + 2 * tc::kStages + 4;
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < tc::kStages; ++s) {
+        tc::mbar_init(tc::smem_u32(&L.bars[s]), 1);
+        tc::mbar_init(tc::smem_u32(&L.bars[tc::kStages + s]), 1);
+        L.sh->issued[s] = -1;
+      }
+      for (int b = 0; b < 2; ++b) {
+        tc::mbar_init(tc::smem_u32(&L.bars[2 * tc::kStages + b]), 1);
+        tc::mbar_init(tc::smem_u32(&L.bars[2 * tc::kStages + 2 + b]), 4);
+      }
+      tc::mbar_init(tc::smem_u32(drain), 1);
+      L.sh->p_stage = 0;
+      L.sh->p_phase = 0;
+      L.sh->m_stage = 0;
+      L.sh->m_phase = 0;
+      L.sh->m_seg = 0;
+      L.sh->m_any = 0;
+      for (int q = 0; q < 4; ++q) L.sh->e_seg[q] = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       tc::smem_u32(&L.sh->tmem)),
+                   "r"(S::kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+
+    solve_body<P, VEC, POL>(prm, uni, &L);
+
+    // teardown: this CTA's copies and MMAs complete before TMEM is freed
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < tc::kStages; ++s)
+        if (L.sh->issued[s] >= 0)
+          mbar_wait_drain(tc::smem_u32(&L.bars[s]), (uint32_t)L.sh->issued[s], prm.timeout_ns);
+    }
+    if (threadIdx.x == 32 && L.sh->m_any) {
+      tc::mma_commit(tc::smem_u32(drain));
+      mbar_wait_drain(tc::smem_u32(drain), 0u, prm.timeout_ns);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 1) {
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(L.sh->tmem),
+                   "r"(S::kTmemCols)
+                   : "memory");
+    }
+  }
+}
+
+template <int P>
+constexpr size_t vs_bytes() {
+  return 2 * sizeof(double) * (size_t)P * Tile<P>::VSTR;
+}
+
+// Dynamic shared memory of fp64_kernel<P, *, POL>.
+template <int P, int POL>
+constexpr size_t solver_smem_bytes() {
+  size_t b = vs_bytes<P>() > sizeof(SerialSmem) ? vs_bytes<P>() : sizeof(SerialSmem);
+  if (b < vs_bytes<1>()) b = vs_bytes<1>();  // CHECK / REFINE use the P = 1 tile
+  b = (b + 15) & ~size_t(15);
+  if constexpr (POL == POL_FP64) {
+    return b;
+  } else {
+    return LpLayout<LpCfg<POL>::KIND, LpNP<P>::value>::kBytes + b;
+  }
+}
+
+template <int P, bool VEC, int POL>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(&fp64_kernel<P, VEC, POL>);
+}
+
+}  // namespace
+}  // namespace ccg

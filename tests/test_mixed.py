@@ -1,0 +1,88 @@
+"""GPU tests of the mixed-precision solve: FP64 refinement around inner cCG
+solves whose block products run on the tensor cores (BF16 or FP8 A).
+
+On systems where the quantised matrix is close enough to A for the
+conditioning (kappa * u < 1, u = 2^-9 for BF16, 2^-4 for FP8), refinement must
+reach the FP64 target: true relative residual <= 1e-10 and
+||x - x_oracle|| / ||x_oracle|| <= 1e-8 against the FP64 oracle.  Where it
+cannot (ill-conditioned kernel matrices), the solve must say so
+(CCG_NOT_CONVERGED) and report the residual of the x it returns truthfully.
+"""
+import numpy as np
+import pytest
+
+from paper_1204_0069_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1204_0069_gb300 import build as B
+    B.build()
+    import oracle
+    oracle.build()
+    from paper_1204_0069_gb300 import ccg
+    return dict(torch=torch, ccg=ccg, oracle=oracle)
+
+
+def solve(env, A, b, p, precision, tol=1e-10, inner_tol=0.0):
+    torch, ccg = env["torch"], env["ccg"]
+    n = b.shape[0]
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with ccg.Solver(precision=precision, inner_tol=inner_tol) as s:
+        r = s.solve(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), x, p=p, tol=tol,
+                    maxit=20 * n)
+    return r, x.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision,shift,n,p", [
+    (2, 0.5, 1024, 4), (2, 0.5, 1500, 8), (2, 0.5, 777, 16), (2, 0.5, 640, 32),
+    (3, 2.0, 1024, 4), (3, 2.0, 900, 8)], ids=["bf16-n1024-p4", "bf16-n1500-p8",
+                                               "bf16-n777-p16", "bf16-n640-p32",
+                                               "fp8-n1024-p4", "fp8-n900-p8"])
+def test_mixed_reaches_fp64_accuracy(env, precision, shift, n, p):
+    A, b = wl.gram_shift(n, seed=n + p, shift=shift)
+    r, x = solve(env, A, b, p, precision)
+    assert r.status == 0, r
+    relres = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    assert relres <= 1e-10 * 1.01, relres
+    assert abs(relres - r.relres_true) <= 1e-3 * relres + 1e-16
+    X0 = env["oracle"].initial_block(n, p, None, 1.0, 0)
+    ref = env["oracle"].ccg(A, b, X0, 1e-10, 20 * n, nthreads=8)
+    err = np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"])
+    assert err <= 1e-8, err
+    assert r.outer_steps >= 2 and r.iterations > 0
+
+
+def test_mixed_reports_truthfully_when_refinement_stalls(env):
+    """Exponential kernel, kappa ~ 1e4: BF16 A is too coarse for plain
+    refinement to reach 1e-10; the status and residual must say so."""
+    A, b = wl.exp_kernel(1024, seed=1, length=0.2, nugget=1e-2)
+    r, x = solve(env, A, b, 8, 2)
+    relres = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    assert abs(relres - r.relres_true) <= 1e-3 * relres
+    if r.status == 0:
+        assert relres <= 1e-10 * 1.01
+    else:
+        assert r.status == 1 and relres > 1e-10
+
+
+def test_prequantised_matrix_reused_across_solves(env):
+    torch, ccg = env["torch"], env["ccg"]
+    n, p = 1200, 8
+    A, b = wl.gram_shift(n, seed=3, shift=0.5)
+    dA = torch.from_numpy(A).cuda()
+    with ccg.Solver() as s:
+        m = s.lowp_matrix(dA, ccg.LOWP_BF16)
+        for k in range(2):
+            bb = torch.from_numpy(b * (k + 1)).cuda()
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            r = s.solve_mixed(m, dA, bb, x, p=p, tol=1e-10, maxit=20 * n)
+            assert r.status == 0
+            xs = x.cpu().numpy()
+            assert np.linalg.norm(b * (k + 1) - A @ xs) / np.linalg.norm(b * (k + 1)) <= 1.01e-10
+        m.close()
