@@ -233,7 +233,8 @@ def mixed_lines(ccg, dev, stream, A, b, p, steps, tol=TOL):
     dA = torch.from_numpy(A).to(dev)
     db = torch.from_numpy(b).to(dev)
     out = {}
-    for name, prec in [("fp64", ccg.FP64), ("bf16_ir", ccg.BF16_IR), ("fp8_ir", ccg.FP8_IR)]:
+    for name, prec in [("fp64", ccg.FP64), ("fp32_ir", ccg.FP32_IR), ("bf16_ir", ccg.BF16_IR),
+                       ("fp8_ir", ccg.FP8_IR)]:
         x = torch.zeros(n, dtype=torch.float64, device=dev)
         with ccg.Solver(stream=stream.cuda_stream, precision=prec) as s:
             s.solve(dA, db, x, p=p, tol=tol, maxit=20 * n)      # warm-up
@@ -251,9 +252,87 @@ def mixed_lines(ccg, dev, stream, A, b, p, steps, tol=TOL):
         out[name] = {"solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t, "status": r.status_name,
                      "relres_true": relres, "iterations": r.iterations,
                      "outer_steps": r.outer_steps}
-    out["speedup_bf16_vs_fp64"] = out["bf16_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"]
-    out["speedup_fp8_vs_fp64"] = out["fp8_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    for k in ("fp32_ir", "bf16_ir", "fp8_ir"):
+        out[f"speedup_{k}_vs_fp64"] = (out[k]["solves_per_s"] / out["fp64"]["solves_per_s"]
+                                       if out[k]["status"] == "CCG_OK" else None)
     return out
+
+
+def batched_line(ccg, dev, stream, count=4096, p=4, seed=3):
+    """4096 independent systems, n log-uniform in [32, 1024], A = G G^T / n +
+    s I with s ~ U(0.05, 1), b ~ N(0, 1) (generated on the device), FP64,
+    one persistent launch."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    sizes = [int(v) for v in np.round(np.exp(rng.uniform(np.log(32), np.log(1024), count)))]
+    shifts = rng.uniform(0.05, 1.0, count)
+    a_off, v_off, at, vt = ccg.batch_offsets(sizes)
+    Ap = torch.zeros(at, dtype=torch.float64, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    for n, sh, ao in zip(sizes, shifts, a_off):
+        G = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+        ld = n + (n & 1)
+        blk = Ap[ao:ao + n * ld].view(n, ld)
+        blk[:, :n] = G @ G.T / n
+        blk.diagonal().add_(float(sh))
+    bp = torch.randn(vt, dtype=torch.float64, device=dev, generator=g)
+    x = torch.zeros_like(bp)
+    with ccg.Solver(stream=stream.cuda_stream) as s:
+        s.solve_batched(sizes, Ap, bp, x, p=p, tol=TOL, maxit=20000)   # warm-up
+        summ, st, it, rr = s.solve_batched(sizes, Ap, bp, x, p=p, tol=TOL, maxit=20000)
+    nsq = float(np.sum(np.array(sizes, dtype=np.float64) ** 2))
+    t = summ.device_ms / 1e3
+    flops = float(np.sum(2.0 * np.array(sizes, dtype=np.float64) ** 2 * p * it))
+    return {"workload": f"{count} systems, n log-uniform [32, 1024], A = G G^T/n + U(0.05,1) I, "
+                        f"p = {p}, FP64, one launch", "systems": count,
+            "solves_per_s": count / t, "ms": summ.device_ms, "status": summ.status_name,
+            "all_ok": bool(np.all(st == 0)), "max_relres": float(np.max(rr)),
+            "iterations_total": int(np.sum(it)), "fp64_tflops": flops / t / 1e12,
+            "a_bytes": 8.0 * nsq, "ctas": summ.ctas}
+
+
+def serving_line(ccg, dev, precision, count=48, rate=2000.0, seed=4, workers=8):
+    """Poisson arrivals (mean 2000/s) of SPD solves with A drawn from a pool of
+    16 device-resident exponential-kernel matrices (n log-uniform in
+    [256, 16384], length U(0.05, 0.5), nugget 10^U(-4, -1)), tol in
+    {1e-6, 1e-10}, p = 8, budget 150 GB.  Latency = completion - arrival."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    pool = []
+    for k in range(16):
+        n = int(np.round(np.exp(rng.uniform(np.log(256), np.log(16384)))))
+        A = device_exp_kernel(n, 1000 + k, float(rng.uniform(0.05, 0.5)),
+                              float(10 ** rng.uniform(-4, -1)), dev)
+        pool.append(A)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+    picks = rng.integers(0, len(pool), count)
+    tols = rng.choice([1e-6, 1e-10], count)
+    bs = [torch.randn(pool[k].shape[0], dtype=torch.float64, device=dev) for k in picks]
+    xs = [torch.zeros_like(b) for b in bs]
+    torch.cuda.synchronize()
+    srv = ccg.Server(workers=workers, precision=precision, budget_bytes=150e9)
+    t0 = srv.stats()["now_ms"]
+    got = {}
+    k = 0
+    while len(got) < count:
+        now = srv.stats()["now_ms"] - t0
+        while k < count and arrivals[k] * 1e3 <= now:
+            srv.submit(k, pool[picks[k]], bs[k], xs[k], p=8, tol=float(tols[k]), maxit=50000)
+            k += 1
+        for r in srv.poll(64, wait_ms=1):
+            got[r["id"]] = r
+    peak = srv.stats()
+    srv.close()
+    lat = np.array([got[i]["done_ms"] - (t0 + arrivals[i] * 1e3) for i in range(count)])
+    span = max(r["done_ms"] for r in got.values()) - t0
+    ok = sum(1 for r in got.values() if r["status"] == 0)
+    return {"requests": count, "ok": ok, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "solves_per_s": count / (span / 1e3),
+            "peak_in_flight": peak["peak_in_flight"],
+            "peak_reserved_gb": peak["peak_reserved_bytes"] / 1e9}
 
 
 def run_reference(args, rank, world):
@@ -409,7 +488,7 @@ def main():
                "h2d_bytes_per_step": int(A.nbytes + b.nbytes),
                "d2h_bytes_per_step": int(8 * n + 192)}
 
-    mixed = lowp = None
+    mixed = lowp = batched = serving = None
     if rank == 0 and not args.no_mixed:
         from paper_1204_0069_gb300 import workloads as wl
         peaks0 = measured_peaks()
@@ -419,6 +498,12 @@ def main():
         mixed["gram_shift_n8192"] = mixed_lines(ccg, dev, stream, Ag, bg, p, 3)
         mixed["gram_shift_n8192"]["workload"] = ("A = G G^T / n + 0.5 I, G ~ N(0,1), n = 8192 "
                                                  "(batching family, seed 3), p = 8")
+        batched = batched_line(ccg, dev, stream)
+        serving = {"workload": ("Poisson(2000/s) arrivals, A from a pool of 16 device-resident "
+                                "exponential-kernel matrices, n log-uniform [256, 16384], "
+                                "tol {1e-6, 1e-10}, p = 8, 8 workers, budget 150 GB"),
+                   "fp64": serving_line(ccg, dev, ccg.FP64),
+                   "fp32_ir": serving_line(ccg, dev, ccg.FP32_IR)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -460,6 +545,10 @@ def main():
             line["lowp_apass"] = lowp
         if mixed is not None:
             line["mixed"] = mixed
+        if batched is not None:
+            line["batched"] = batched
+        if serving is not None:
+            line["serving"] = serving
         if e2e is not None:
             line["e2e"] = e2e
         if cpu is not None:

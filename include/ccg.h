@@ -57,6 +57,8 @@ typedef enum {
 
 typedef enum {
     CCG_FP64 = 0,            /* every operation in FP64                      */
+    CCG_FP32_IR = 1,         /* A in FP32, products as three TF32 terms on the
+                                tensor cores, FP64 refinement                 */
     CCG_BF16_IR = 2,         /* A in BF16 on the tensor cores, FP64 refinement */
     CCG_FP8_IR = 3           /* A in FP8 E4M3 on the tensor cores, FP64 refinement */
 } ccg_precision;
@@ -74,7 +76,8 @@ typedef struct {
     double barrier_timeout_ms;  /* in-kernel barrier wait limit; 10000 ms    */
     int max_ctas;               /* 0 = one CTA per SM; else an upper bound   */
     double inner_tol;           /* mixed precision: relative tolerance of each
-                                   inner solve; 0 = 1e-2 (BF16), 1e-1 (FP8)  */
+                                   inner solve; 0 = 1e-4 (FP32), 1e-2 (BF16),
+                                   1e-1 (FP8)                                 */
     int max_outer;              /* mixed precision: refinement steps; 0 = 60 */
 } ccg_config;
 
@@ -122,8 +125,8 @@ int ccg_destroy(ccg_handle* handle);
  *               returned agent, ||b - A x||/||b|| in FP64, is <= tol.
  *   maxit     : maximum cCG iterations (>= 0).
  *   x_out     : n values; receives the agent with the smallest residual.
- * With cfg.precision CCG_BF16_IR or CCG_FP8_IR the call quantises A into a
- * handle-owned copy and runs ccg_solve_mixed (see there).
+ * With cfg.precision CCG_FP32_IR, CCG_BF16_IR or CCG_FP8_IR the call quantises
+ * A into a handle-owned copy and runs ccg_solve_mixed (see there).
  *   res       : optional result record (host memory).
  * Errors: CCG_ERR_INVALID (n < 1, p out of range, tol <= 0, maxit < 0,
  * lda < n, NULL pointer), CCG_ERR_NOT_SPD, CCG_ERR_NUMERICAL, CCG_ERR_OOM,
@@ -167,8 +170,12 @@ int ccg_selftest_barrier_timeout(ccg_handle* handle, double timeout_ms);
 /* Storage formats of a quantised copy of A. */
 typedef enum {
     CCG_LOWP_BF16 = 0,      /* bfloat16, round to nearest (2 bytes/entry)      */
-    CCG_LOWP_FP8_E4M3 = 1   /* FP8 E4M3, one FP32 scale per row: A_ij ~= s_i q_ij,
+    CCG_LOWP_FP8_E4M3 = 1,  /* FP8 E4M3, one FP32 scale per row: A_ij ~= s_i q_ij,
                                s_i = max_j |A_ij| / 448 (1 byte/entry)        */
+    CCG_LOWP_FP32 = 2       /* FP32 (4 bytes/entry); the tensor cores form
+                               A_hi D_hi + A_hi D_lo + A_lo D_hi with TF32
+                               halves (A_lo = A - tf32(A)), about 2^-21
+                               relative error per product                     */
 } ccg_lowp_format;
 
 /* Opaque quantised matrix (device memory owned by the object). */
@@ -217,6 +224,100 @@ int64_t ccg_lowp_bytes(const ccg_lowp_matrix* m);
 
 /* Free the quantised matrix.  NULL-safe. */
 int ccg_lowp_destroy(ccg_lowp_matrix* m);
+
+/* ---- Many independent systems in one launch ------------------------------ */
+
+/*
+ * Solve `count` independent SPD systems A_i x_i = b_i, each with p agents
+ * (Algorithm 2 with the deflation of Algorithm 3, FP64), in one persistent
+ * launch: every CTA takes the next system from a queue ordered largest
+ * first and solves it alone, so systems of uneven size keep all SMs busy.
+ *
+ *   n[i]      : sizes (host array), 1 <= p <= n[i].
+ *   A         : device buffer, systems packed one after another: A_i is
+ *               n_i x n_i row-major with leading dimension ld_i = n_i rounded
+ *               up to even, starting at element sum_{j<i} n_j ld_j.
+ *   b, x_out  : device buffers, b_i and x_i packed at element sum_{j<i} n_j.
+ *   status, iterations, relres : optional host arrays of `count` entries
+ *               (per-system ccg_status, iterations, true relative residual).
+ *   summary   : optional: status = CCG_OK if every system converged, else the
+ *               first non-OK status; iterations = sum over systems;
+ *               device_ms = time of the launch; ctas = grid size.
+ * Each system uses the handle's configuration (x0 = 0 with the initial-block
+ * spread, residual replacement, rank tolerance).  Errors: CCG_ERR_INVALID
+ * (count < 0, bad sizes, host pointers for A, b, x_out), CCG_ERR_OOM,
+ * CCG_ERR_CUDA.
+ */
+int ccg_solve_batched(ccg_handle* handle, int64_t count, const int64_t* n, const double* A,
+                      const double* b, int p, double tol, int maxit, double* x_out,
+                      int* status, int* iterations, double* relres, ccg_result* summary);
+
+/* ---- Serving: a stream of solve requests --------------------------------- */
+
+/* Opaque server. */
+typedef struct ccg_server_s ccg_server;
+
+typedef struct {
+    int device;             /* CUDA device                                      */
+    int workers;            /* concurrent solves (worker threads, streams); 8   */
+    int precision;          /* ccg_precision of every solve; CCG_FP64            */
+    double budget_bytes;    /* device bytes the admitted requests may hold; 150e9 */
+    int ctas_per_worker;    /* SM share of one solve; 0 = SMs / workers          */
+} ccg_server_config;
+
+typedef struct {
+    int64_t id;             /* the id given to ccg_server_submit                */
+    int status;             /* ccg_status of the solve                          */
+    int iterations;
+    int outer_steps;        /* mixed precision: refinement steps               */
+    int worker;
+    int ctas;
+    double relres_true;     /* ||b - A x|| / ||b|| in FP64                       */
+    double submit_ms;       /* server clock (ms since ccg_server_create)        */
+    double admit_ms;        /* admitted: a worker and the memory were free     */
+    double done_ms;         /* solution in x_out                               */
+} ccg_server_result;
+
+typedef struct {
+    int64_t queued, completed;
+    int in_flight, peak_in_flight, ctas_per_worker;
+    double reserved_bytes, peak_reserved_bytes, now_ms;
+} ccg_server_stats_t;
+
+/* Fill *cfg with the defaults listed above. */
+void ccg_server_config_init(ccg_server_config* cfg);
+
+/*
+ * Start a server: `workers` threads, each with its own handle and stream and
+ * a fixed share of the SMs.  Requests are admitted in arrival order, first
+ * fit: a free worker takes the oldest queued request whose device memory
+ * (its matrix, kept resident for the request's lifetime, plus workspace and,
+ * for mixed precision, the quantised copy) fits in the budget left by the
+ * running requests.  Requests admitted while others run execute concurrently
+ * on the device.  A request's grid depends only on its size and the worker
+ * share, so its result does not depend on what else is running.
+ */
+int ccg_server_create(const ccg_server_config* cfg, ccg_server** out);
+
+/*
+ * Queue the solve of A x = b (device pointers, A n x n with lda; x_out n
+ * values) with p agents to relative tolerance tol (ccg_solve semantics, x0 =
+ * 0).  The buffers must stay valid until the request's result is polled.
+ * Returns at once: CCG_OK, CCG_ERR_INVALID, or CCG_ERR_OOM if the request can
+ * never fit the budget.
+ */
+int ccg_server_submit(ccg_server* server, int64_t id, int64_t n, const double* A, int64_t lda,
+                      const double* b, double* x_out, int p, double tol, int maxit);
+
+/* Move up to `max` finished results into out[], waiting up to wait_ms for the
+ * first one; returns how many were written. */
+int ccg_server_poll(ccg_server* server, ccg_server_result* out, int max, int wait_ms);
+
+/* Current queue, in-flight, completed and memory figures. */
+int ccg_server_stats(ccg_server* server, ccg_server_stats_t* stats);
+
+/* Finish the queued and running requests, then stop.  NULL-safe. */
+int ccg_server_destroy(ccg_server* server);
 
 /* ---- Solve without any device allocation --------------------------------- */
 

@@ -22,10 +22,12 @@ OK, NOT_CONVERGED = 0, 1
 EXPORTED = ["ccg_config_init", "ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
             "ccg_block_product", "ccg_selftest_barrier_timeout", "ccg_status_string",
             "ccg_version", "ccg_lowp_create", "ccg_lowp_block_product", "ccg_lowp_bytes",
-            "ccg_lowp_destroy", "ccg_solve_noalloc", "ccg_solve_mixed"]
-FP64, BF16_IR, FP8_IR = 0, 2, 3
+            "ccg_lowp_destroy", "ccg_solve_noalloc", "ccg_solve_mixed", "ccg_solve_batched",
+            "ccg_server_config_init", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
+            "ccg_server_stats", "ccg_server_destroy"]
+FP64, FP32_IR, BF16_IR, FP8_IR = 0, 1, 2, 3
 NOALLOC_MAX_NP = 131072
-LOWP_BF16, LOWP_FP8_E4M3 = 0, 1
+LOWP_BF16, LOWP_FP8_E4M3, LOWP_FP32 = 0, 1, 2
 
 
 class Config(ctypes.Structure):
@@ -35,6 +37,25 @@ class Config(ctypes.Structure):
                 ("residual_replacement", ctypes.c_int),
                 ("barrier_timeout_ms", ctypes.c_double), ("max_ctas", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("workers", ctypes.c_int), ("precision", ctypes.c_int),
+                ("budget_bytes", ctypes.c_double), ("ctas_per_worker", ctypes.c_int)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("outer_steps", ctypes.c_int), ("worker", ctypes.c_int), ("ctas", ctypes.c_int),
+                ("relres_true", ctypes.c_double), ("submit_ms", ctypes.c_double),
+                ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("in_flight", ctypes.c_int), ("peak_in_flight", ctypes.c_int),
+                ("ctas_per_worker", ctypes.c_int), ("reserved_bytes", ctypes.c_double),
+                ("peak_reserved_bytes", ctypes.c_double), ("now_ms", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -91,6 +112,20 @@ def lib():
         L.ccg_solve_mixed.argtypes = [_VP, _VP, _I64, _VP, _I64, _VP, _VP, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_int, _VP, ctypes.POINTER(Result)]
         L.ccg_solve_mixed.restype = ctypes.c_int
+        L.ccg_solve_batched.argtypes = [_VP, _I64, _VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.POINTER(Result)]
+        L.ccg_solve_batched.restype = ctypes.c_int
+        L.ccg_server_config_init.argtypes = [ctypes.POINTER(ServerConfig)]
+        L.ccg_server_config_init.restype = None
+        L.ccg_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_VP)]
+        L.ccg_server_submit.argtypes = [_VP, ctypes.c_int64, _I64, _VP, _I64, _VP, _VP,
+                                        ctypes.c_int, ctypes.c_double, ctypes.c_int]
+        L.ccg_server_poll.argtypes = [_VP, ctypes.POINTER(ServerResult), ctypes.c_int, ctypes.c_int]
+        L.ccg_server_stats.argtypes = [_VP, ctypes.POINTER(ServerStats)]
+        L.ccg_server_destroy.argtypes = [_VP]
+        for name in ["ccg_server_create", "ccg_server_submit", "ccg_server_poll",
+                     "ccg_server_stats", "ccg_server_destroy"]:
+            getattr(L, name).restype = ctypes.c_int
         for name in ["ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
                      "ccg_block_product", "ccg_selftest_barrier_timeout", "ccg_lowp_create",
                      "ccg_lowp_block_product", "ccg_lowp_destroy"]:
@@ -231,6 +266,20 @@ class Solver:
                                   float(tol), int(maxit), _ptr(x_out), ctypes.byref(r))
         return self._res(r)
 
+    def solve_batched(self, sizes, A_packed, b_packed, x_packed, p: int, tol: float, maxit: int):
+        """ccg_solve_batched over systems packed as described in include/ccg.h
+        (see pack_batch).  Returns (summary, status[], iterations[], relres[])."""
+        cnt = len(sizes)
+        nn = np.ascontiguousarray(sizes, dtype=np.int64)
+        st = np.zeros(cnt, dtype=np.int32)
+        it = np.zeros(cnt, dtype=np.int32)
+        rr = np.zeros(cnt, dtype=np.float64)
+        r = Result()
+        self._lib.ccg_solve_batched(self._h, cnt, nn.ctypes.data, _ptr(A_packed), _ptr(b_packed),
+                                    int(p), float(tol), int(maxit), _ptr(x_packed),
+                                    st.ctypes.data, it.ctypes.data, rr.ctypes.data, ctypes.byref(r))
+        return self._res(r), st, it, rr
+
     def lowp_matrix(self, A, fmt: int, lda=None) -> "LowpMatrix":
         """Quantised copy of A (ccg_lowp_create) on this handle's device."""
         n = int(A.shape[0])
@@ -272,6 +321,64 @@ class LowpMatrix:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """A serving loop (ccg_server_create): submit requests, poll results."""
+
+    def __init__(self, device: int = 0, workers: int = 8, precision: int = 0,
+                 budget_bytes: float = 150e9, ctas_per_worker: int = 0):
+        L = lib()
+        c = ServerConfig()
+        L.ccg_server_config_init(ctypes.byref(c))
+        c.device, c.workers, c.precision = device, workers, precision
+        c.budget_bytes, c.ctas_per_worker = budget_bytes, ctas_per_worker
+        h = _VP()
+        rc = L.ccg_server_create(ctypes.byref(c), ctypes.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"ccg_server_create failed: {STATUS.get(rc, rc)}")
+        self._h, self._lib = h, L
+
+    def submit(self, rid: int, A, b, x_out, p: int, tol: float, maxit: int, lda=None) -> int:
+        n = int(b.shape[0])
+        lda = int(A.shape[1]) if lda is None else lda
+        return int(self._lib.ccg_server_submit(self._h, int(rid), n, _ptr(A), lda, _ptr(b),
+                                               _ptr(x_out), int(p), float(tol), int(maxit)))
+
+    def poll(self, max_results: int = 64, wait_ms: int = 0):
+        buf = (ServerResult * max_results)()
+        k = self._lib.ccg_server_poll(self._h, buf, max_results, int(wait_ms))
+        return [{f: getattr(buf[i], f) for f, _ in ServerResult._fields_} for i in range(max(k, 0))]
+
+    def stats(self):
+        st = ServerStats()
+        self._lib.ccg_server_stats(self._h, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ccg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_offsets(sizes):
+    """Element offsets of the packed batch layout of ccg_solve_batched: A_i at
+    sum_{j<i} n_j ld_j (ld_j = n_j rounded up to even), b_i / x_i at
+    sum_{j<i} n_j.  Returns (a_off, v_off, a_total, v_total)."""
+    a_off, v_off = [], []
+    a = v = 0
+    for nn in sizes:
+        a_off.append(a)
+        v_off.append(v)
+        a += nn * (nn + (nn & 1))
+        v += nn
+    return a_off, v_off, a, v
 
 
 def solve_noalloc(A, b, x_out, p: int, tol: float, maxit: int, x0=None, device: int = 0,

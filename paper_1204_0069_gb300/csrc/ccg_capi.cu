@@ -215,7 +215,8 @@ int ccg_create(ccg_handle** out, const ccg_config* cfg) {
   if (cfg) c = *cfg;
   else ccg_config_init(&c);
   if (!(c.rank_tol > 0.0) || !(c.barrier_timeout_ms > 0.0) ||
-      (c.precision != CCG_FP64 && c.precision != CCG_BF16_IR && c.precision != CCG_FP8_IR) ||
+      (c.precision != CCG_FP64 && c.precision != CCG_FP32_IR && c.precision != CCG_BF16_IR &&
+       c.precision != CCG_FP8_IR) ||
       c.max_ctas < 0 || c.inner_tol < 0.0 || c.max_outer < 0)
     return CCG_ERR_INVALID;
   int ndev = 0;
@@ -261,19 +262,38 @@ int ccg_destroy(ccg_handle* h) {
 int ccg_solve(ccg_handle* h, int64_t n, const double* A, int64_t lda, const double* b,
               const double* x0, int p, double tol, int maxit, double* x_out, ccg_result* res) {
   if (h && h->cfg.precision != CCG_FP64) {
-    // mixed precision: quantise A into the handle's copy, then refine in FP64
-    if (h->lp) {
-      ccg_lowp_destroy(h->lp);
-      h->lp = nullptr;
-    }
-    const int fmt = h->cfg.precision == CCG_BF16_IR ? CCG_LOWP_BF16 : CCG_LOWP_FP8_E4M3;
+    // mixed precision: quantise A into a copy for this solve, refine in FP64
+    const int fmt = h->cfg.precision == CCG_BF16_IR   ? CCG_LOWP_BF16
+                    : h->cfg.precision == CCG_FP32_IR ? CCG_LOWP_FP32
+                                                      : CCG_LOWP_FP8_E4M3;
     if (res) std::memset(res, 0, sizeof(*res));
-    const int rc = ccg_lowp_create(h, fmt, n, A, lda, &h->lp);
+    if (n < 1 || lda < n || !A || !aligned(A, 8)) {
+      if (res) res->status = CCG_ERR_INVALID;
+      return CCG_ERR_INVALID;
+    }
+    DeviceGuard guard(h->device);
+    const double* dA = A;
+    int64_t ldA = lda;
+    if (!is_device_ptr(A)) {
+      // host A: ccg_solve_mixed stages it; the quantiser needs a device copy too
+      const int rc0 = ensure(&h->stage, &h->stage_bytes, (size_t)n * n * sizeof(double));
+      if (rc0 != CCG_OK) return rc0;
+      cudaError_t e = cudaMemcpy2DAsync(h->stage, n * sizeof(double), A, lda * sizeof(double),
+                                        n * sizeof(double), n, cudaMemcpyHostToDevice, h->stream);
+      if (e != cudaSuccess) return map_cuda(e);
+      dA = reinterpret_cast<const double*>(h->stage);
+      ldA = n;
+    }
+    ccg_lowp_matrix_s* m = nullptr;
+    const int rc = lowp_create_async(h, fmt, n, dA, ldA, &m);
     if (rc != CCG_OK) {
       if (res) res->status = rc;
       return rc;
     }
-    return ccg_solve_mixed(h, h->lp, n, A, lda, b, x0, p, tol, maxit, x_out, res);
+    // (host A is staged again by the mixed driver; a device A is used in place)
+    const int st = ccg_solve_mixed(h, m, n, A, lda, b, x0, p, tol, maxit, x_out, res);
+    lowp_destroy_async(h, m);
+    return st;
   }
   return solve_impl(h, n, A, lda, b, x0, nullptr, p, tol, maxit, x_out, nullptr, res);
 }

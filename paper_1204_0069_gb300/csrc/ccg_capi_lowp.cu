@@ -3,11 +3,13 @@
 // checks, device buffers and launches only; the arithmetic is in ccg_lowp.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <new>
 
 #include "ccg.h"
 #include "ccg_handle.h"
+#include "ccg_internal.h"
 #include "ccg_lowp.h"
 
 using namespace ccg_host;
@@ -15,9 +17,111 @@ using namespace ccg_host;
 
 namespace {
 
-int lp_kind(int format) { return format == CCG_LOWP_BF16 ? ccg::lp::KIND_BF16 : ccg::lp::KIND_FP8; }
+int lp_kind(int format) {
+  return format == CCG_LOWP_BF16 ? ccg::lp::KIND_BF16
+         : format == CCG_LOWP_FP32 ? ccg::lp::KIND_TF32X3
+                                   : ccg::lp::KIND_FP8;
+}
+
+size_t lp_esize(int format) {
+  return format == CCG_LOWP_BF16 ? 2 : format == CCG_LOWP_FP32 ? 4 : 1;
+}
+
+// W = A_lp V through the persistent solver kernel's tensor-core A-pass (the
+// code path of the inner solves), used for the FP32 (TF32x3) format.
+int block_product_persistent(ccg_handle* h, const ccg_lowp_matrix_s* m, const double* dV, int q,
+                             double* dW, float* device_ms) {
+  const int64_t n = m->n;
+  const int P = ccg::p_bucket(q);
+  const int NP = P <= 16 ? 16 : 32;
+  const int NB = 2 * NP;
+  const int64_t ldk = ccg::lp::ld_elems(n);
+  const int64_t T = (n + 127) / 128;
+  const int pol = ccg::POL_TF32X3;
+  int64_t g = std::min<int64_t>(h->num_sms, (n + ccg::kWarps - 1) / ccg::kWarps);
+  if (h->cfg.max_ctas > 0) g = std::min<int64_t>(g, h->cfg.max_ctas);
+  const int G = (int)std::max<int64_t>(1, g);
+  if (ccg::fp64_ctas_per_sm(P, true, pol) < 1) return CCG_ERR_CUDA;
+  int rc = ensure(&h->ws, &h->ws_bytes,
+                  Carve::need({(size_t)G * ccg::kPartStride * sizeof(double),
+                               sizeof(ccg::DevState), (size_t)NB * ldk * sizeof(float),
+                               (size_t)(G + T) * 128 * NP * sizeof(float)}));
+  if (rc != CCG_OK) return rc;
+  Carve wc(h->ws);
+  ccg::Params prm{};
+  prm.n = n;
+  prm.lda = n;
+  prm.part = wc.take<double>((size_t)G * ccg::kPartStride);
+  prm.st = wc.take<ccg::DevState>(1);
+  prm.lp_dq = wc.take<float>((size_t)NB * ldk);
+  prm.lp_part = wc.take<float>((size_t)(G + T) * 128 * NP);
+  prm.mode = ccg::MODE_BLOCK_PRODUCT;
+  prm.timeout_ns = (long long)(h->cfg.barrier_timeout_ms * 1e6);
+  prm.expected_ctas = (unsigned)G;
+  prm.V = dV;
+  prm.Wout = dW;
+  prm.q = q;
+  prm.p = q;
+  prm.lp_kelems = 32;
+  prm.lp_kc = (int)((n + 31) / 32);
+  prm.lp_units = T * prm.lp_kc;
+  prm.lp_ldk = ldk;
+  if (!ccg::lp::make_tensor_map(&prm.lp_tmA, m->q, ccg::lp::KIND_TF32X3, n, n, m->ldq, 128) ||
+      !ccg::lp::make_tensor_map(&prm.lp_tmB, prm.lp_dq, ccg::lp::KIND_TF32X3, NB, n, ldk, NB))
+    return CCG_ERR_CUDA;
+  std::memset(h->h_state, 0, sizeof(ccg::DevState));
+  h->h_state->pk = q;
+  cudaStream_t s = h->stream;
+  cudaError_t e = cudaMemcpyAsync(prm.st, h->h_state, sizeof(ccg::DevState), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev0, s);
+  if (e == cudaSuccess) e = ccg::launch_fp64(prm, P, true, G, s, pol);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev1, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_state, prm.st, sizeof(ccg::DevState), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return map_cuda(e);
+  if (device_ms) cudaEventElapsedTime(device_ms, h->ev0, h->ev1);
+  return h->h_state->error != 0 ? h->h_state->error : CCG_OK;
+}
 
 }  // namespace
+
+namespace ccg_host {
+
+// Quantised copy of A for one solve, in stream-ordered memory of the
+// handle's stream (returned to the pool without a device-wide sync).
+int lowp_create_async(ccg_handle* h, int format, int64_t n, const double* A, int64_t lda,
+                      ccg_lowp_matrix_s** out) {
+  *out = nullptr;
+  cudaStream_t s = h->stream;
+  ccg_lowp_matrix_s* m = new (std::nothrow) ccg_lowp_matrix_s();
+  if (!m) return CCG_ERR_OOM;
+  m->format = format;
+  m->device = h->device;
+  m->n = n;
+  m->ldq = ccg::lp::ld_elems(n);
+  const size_t qbytes = (size_t)n * (size_t)m->ldq * lp_esize(format);
+  cudaError_t e = cudaMallocAsync(&m->q, qbytes, s);
+  if (e == cudaSuccess && format == CCG_LOWP_FP8_E4M3)
+    e = cudaMallocAsync(reinterpret_cast<void**>(&m->row_scale), (size_t)n * sizeof(float), s);
+  if (e == cudaSuccess) e = ccg::lp::quantize(lp_kind(format), A, lda, n, m->q, m->ldq, m->row_scale, s);
+  if (e != cudaSuccess) {
+    lowp_destroy_async(h, m);
+    return map_cuda(e);
+  }
+  m->bytes = (int64_t)qbytes;
+  *out = m;
+  return CCG_OK;
+}
+
+void lowp_destroy_async(ccg_handle* h, ccg_lowp_matrix_s* m) {
+  if (!m) return;
+  if (m->q) cudaFreeAsync(m->q, h->stream);
+  if (m->row_scale) cudaFreeAsync(m->row_scale, h->stream);
+  delete m;
+}
+
+}  // namespace ccg_host
 
 extern "C" {
 
@@ -25,7 +129,8 @@ int ccg_lowp_create(ccg_handle* h, int format, int64_t n, const double* A, int64
                     ccg_lowp_matrix** out) {
   if (!out) return CCG_ERR_INVALID;
   *out = nullptr;
-  if (!h || !A || n < 1 || lda < n || (format != CCG_LOWP_BF16 && format != CCG_LOWP_FP8_E4M3) ||
+  if (!h || !A || n < 1 || lda < n ||
+      (format != CCG_LOWP_BF16 && format != CCG_LOWP_FP8_E4M3 && format != CCG_LOWP_FP32) ||
       !aligned(A, 8))
     return CCG_ERR_INVALID;
   DeviceGuard guard(h->device);
@@ -47,7 +152,7 @@ int ccg_lowp_create(ccg_handle* h, int format, int64_t n, const double* A, int64
   m->device = h->device;
   m->n = n;
   m->ldq = ccg::lp::ld_elems(n);
-  const size_t esz = (format == CCG_LOWP_BF16) ? 2 : 1;
+  const size_t esz = lp_esize(format);
   const size_t qbytes = (size_t)n * (size_t)m->ldq * esz;
   cudaError_t e = cudaMalloc(&m->q, qbytes);
   if (e == cudaSuccess && format == CCG_LOWP_FP8_E4M3)
@@ -111,6 +216,15 @@ int ccg_lowp_block_product(ccg_handle* h, const ccg_lowp_matrix* m, const double
   }
   if (!w_dev) dW = sc.take<double>(nq);
   if (e != cudaSuccess) return map_cuda(e);
+  if (m->format == CCG_LOWP_FP32) {
+    int rc2 = block_product_persistent(h, m, dV, q, dW, device_ms);
+    if (rc2 == CCG_OK && !w_dev) {
+      e = cudaMemcpyAsync(W, dW, nq * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return map_cuda(e);
+    }
+    return rc2;
+  }
   Carve wc(h->ws);
   void* Vt = wc.take<char>((size_t)NB * ldk * esz);
   unsigned* cmax = wc.take<unsigned>(32);

@@ -29,7 +29,41 @@ void* select_any(int P, bool vec, int pol) {
   return pol == POL_FP64 ? select_kernel(P, vec) : select_kernel_lp(P, pol);
 }
 
+void* select_batch(int P) {
+  switch (P) {
+    case 1: return reinterpret_cast<void*>(&batch_kernel<1>);
+    case 2: return reinterpret_cast<void*>(&batch_kernel<2>);
+    case 4: return reinterpret_cast<void*>(&batch_kernel<4>);
+    case 8: return reinterpret_cast<void*>(&batch_kernel<8>);
+    case 16: return reinterpret_cast<void*>(&batch_kernel<16>);
+    case 32: return reinterpret_cast<void*>(&batch_kernel<32>);
+    default: return nullptr;
+  }
+}
+
 }  // namespace
+
+int batch_ctas_per_sm(int P) {
+  void* fn = select_batch(P);
+  if (!fn) return 0;
+  const size_t smem = fp64_smem_bytes(P, POL_FP64);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_batch(const Params& prm, int P, int ctas, cudaStream_t stream) {
+  void* fn = select_batch(P);
+  if (!fn) return cudaErrorInvalidValue;
+  const size_t smem = fp64_smem_bytes(P, POL_FP64);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  Params local = prm;
+  void* args[] = {&local};
+  return cudaLaunchKernel(fn, dim3(ctas), dim3(kThreads), args, smem, stream);
+}
 
 int p_bucket(int p) {
   int P = 1;

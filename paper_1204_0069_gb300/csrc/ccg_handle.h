@@ -109,4 +109,9 @@ struct Carve {
   }
 };
 
+// Stream-ordered quantised copy for one solve (ccg_capi_lowp.cu).
+int lowp_create_async(ccg_handle* h, int format, int64_t n, const double* A, int64_t lda,
+                      ccg_lowp_matrix_s** out);
+void lowp_destroy_async(ccg_handle* h, ccg_lowp_matrix_s* m);
+
 }  // namespace ccg_host

@@ -40,7 +40,7 @@ enum Mode : int {
 
 // A-pass policy of the persistent kernel: FP64 A on the FP64 pipe, or a
 // quantised A on the tensor cores (inner solves of the mixed-precision path).
-enum Policy : int { POL_FP64 = 0, POL_BF16 = 1, POL_FP8 = 2 };
+enum Policy : int { POL_FP64 = 0, POL_BF16 = 1, POL_FP8 = 2, POL_TF32X3 = 3 };
 
 // Status values mirror ccg_status in include/ccg.h.
 enum Status : int {
@@ -121,6 +121,18 @@ struct Params {
   int q;
   // inner solves (mixed precision): stop on the recurrence residual alone
   int skip_true_check;
+  // CTAs that solve one system together (0 = the whole grid) and this CTA's
+  // rank in its group; the batched solver runs groups of one CTA
+  int group_ctas;
+  int group_rank;
+  // batched solve: systems taken from a queue, one per CTA at a time
+  int64_t batch_count;
+  const int64_t* batch_desc;   // per queued system: n, A offset, vector offset, index
+  int64_t batch_slot_stride;   // doubles of X, R, D0, D1, W workspace per CTA
+  unsigned int* batch_next;    // queue head
+  int* batch_status;
+  int* batch_iters;
+  double* batch_relres;
   // tensor-core A-pass (policy != POL_FP64)
   int lp_kc;               // k-chunks per 128-row tile
   int lp_kelems;           // K elements per chunk
@@ -148,5 +160,8 @@ size_t fp64_smem_bytes(int P, int pol = POL_FP64);
 int fp64_ctas_per_sm(int P, bool vec, int pol = POL_FP64);
 cudaError_t launch_fp64(const Params& prm, int P, bool vec, int ctas,
                         cudaStream_t stream, int pol = POL_FP64);
+// Batched solver (groups of one CTA): occupancy and launch.
+int batch_ctas_per_sm(int P);
+cudaError_t launch_batch(const Params& prm, int P, int ctas, cudaStream_t stream);
 
 }  // namespace ccg

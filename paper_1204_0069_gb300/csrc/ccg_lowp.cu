@@ -244,6 +244,14 @@ __global__ void quant_bf16_kernel(const double* __restrict__ A, int64_t lda, int
     Q[i * ldq + k] = (k < n) ? __double2bfloat16(A[i * lda + k]) : __double2bfloat16(0.0);
 }
 
+// A (FP64) -> FP32 rows of ldq elements (round to nearest).
+__global__ void quant_f32_kernel(const double* __restrict__ A, int64_t lda, int64_t n,
+                                 float* __restrict__ Q, int64_t ldq) {
+  const int64_t i = blockIdx.x;
+  for (int64_t k = threadIdx.x; k < ldq; k += blockDim.x)
+    Q[i * ldq + k] = (k < n) ? (float)A[i * lda + k] : 0.f;
+}
+
 // A -> FP8 E4M3 with a per-row scale s_i = max_k |A_ik| / 448.
 __global__ void quant_fp8_kernel(const double* __restrict__ A, int64_t lda, int64_t n,
                                  uint8_t* __restrict__ Q, int64_t ldq, float* __restrict__ scale) {
@@ -342,12 +350,15 @@ bool make_map(CUtensorMap* m, const void* base, int kind, int64_t rows, int64_t 
               int64_t ld, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
-  const int esz = (kind == KIND_BF16) ? 2 : 1;
+  const int esz = (kind == KIND_BF16) ? 2 : (kind == KIND_TF32X3) ? 4 : 1;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
   cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(m, kind == KIND_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+  const CUtensorMapDataType dt = kind == KIND_BF16    ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : kind == KIND_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                       : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  CUresult r = fn(m, dt,
                   2, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -372,6 +383,8 @@ cudaError_t quantize(int kind, const double* A, int64_t lda, int64_t n, void* Q,
                      float* row_scale, cudaStream_t s) {
   if (kind == KIND_BF16)
     quant_bf16_kernel<<<(unsigned)n, 256, 0, s>>>(A, lda, n, reinterpret_cast<__nv_bfloat16*>(Q), ldq);
+  else if (kind == KIND_TF32X3)
+    quant_f32_kernel<<<(unsigned)n, 256, 0, s>>>(A, lda, n, reinterpret_cast<float*>(Q), ldq);
   else
     quant_fp8_kernel<<<(unsigned)n, 256, 0, s>>>(A, lda, n, reinterpret_cast<uint8_t*>(Q), ldq,
                                                   row_scale);

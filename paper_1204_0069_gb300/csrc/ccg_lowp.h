@@ -9,7 +9,7 @@
 namespace ccg {
 namespace lp {
 
-enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1 };
+enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1, KIND_TF32X3 = 2 };
 
 // Launch description of one stream-K block product.
 struct LpRun {
@@ -30,7 +30,7 @@ struct LpRun {
 int64_t ld_elems(int64_t n);
 // Floats of partial-tile storage for a launch on `ctas` CTAs with N = NP.
 size_t part_floats(int64_t n, int ctas, int NP);
-// A (FP64) -> Q: BF16, or FP8 E4M3 with per-row scales (row_scale, n floats).
+// A (FP64) -> Q: BF16, FP8 E4M3 with per-row scales (row_scale, n floats), or FP32.
 cudaError_t quantize(int kind, const double* A, int64_t lda, int64_t n, void* Q, int64_t ldq,
                      float* row_scale, cudaStream_t s);
 // V (FP64, n x q row-major) -> Vt: NP (BF16) or 2 NP (FP8 hi, lo) rows of ldk

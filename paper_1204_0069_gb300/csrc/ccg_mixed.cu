@@ -75,13 +75,14 @@ extern "C" int ccg_solve_mixed(ccg_handle* h, const ccg_lowp_matrix* m, int64_t 
   cudaStream_t s = h->stream;
 
   const bool fp8 = m->format == CCG_LOWP_FP8_E4M3;
-  const int pol = fp8 ? ccg::POL_FP8 : ccg::POL_BF16;
-  const int kind = fp8 ? ccg::lp::KIND_FP8 : ccg::lp::KIND_BF16;
+  const bool f32 = m->format == CCG_LOWP_FP32;
+  const int pol = fp8 ? ccg::POL_FP8 : f32 ? ccg::POL_TF32X3 : ccg::POL_BF16;
+  const int kind = fp8 ? ccg::lp::KIND_FP8 : f32 ? ccg::lp::KIND_TF32X3 : ccg::lp::KIND_BF16;
   const int P = ccg::p_bucket(p);
   const int NP = P <= 16 ? 16 : 32;
-  const int NB = fp8 ? 2 * NP : NP;
+  const int NB = (fp8 || f32) ? 2 * NP : NP;
   const int64_t ldk = ccg::lp::ld_elems(n);
-  const size_t esz = fp8 ? 1 : 2;
+  const size_t esz = fp8 ? 1 : f32 ? 4 : 2;
   const int G = grid_size(h, n);
   const int64_t T = (n + 127) / 128;
   const size_t np = (size_t)n * p;
@@ -185,7 +186,7 @@ extern "C" int ccg_solve_mixed(ccg_handle* h, const ccg_lowp_matrix* m, int64_t 
   in.timeout_ns = ref.timeout_ns;
   in.expected_ctas = (unsigned)G;
   in.skip_true_check = 1;
-  in.lp_kelems = fp8 ? 128 : 64;
+  in.lp_kelems = (int)(128 / esz);
   in.lp_kc = (int)((n + in.lp_kelems - 1) / in.lp_kelems);
   in.lp_units = T * in.lp_kc;
   in.lp_row_scale = m->row_scale;
@@ -196,7 +197,7 @@ extern "C" int ccg_solve_mixed(ccg_handle* h, const ccg_lowp_matrix* m, int64_t 
       !ccg::lp::make_tensor_map(&in.lp_tmB, dq, kind, NB, n, ldk, NB))
     return fail(CCG_ERR_CUDA);
 
-  const double tin_default = fp8 ? 1e-1 : 1e-2;
+  const double tin_default = fp8 ? 1e-1 : f32 ? 1e-4 : 1e-2;
   const double tin = h->cfg.inner_tol > 0.0 ? h->cfg.inner_tol : tin_default;
   const int max_outer = h->cfg.max_outer > 0 ? h->cfg.max_outer : 60;
 

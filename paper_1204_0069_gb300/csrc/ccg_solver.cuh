@@ -121,8 +121,22 @@ struct SyncShared {
   int flag;
 };
 
+// Size of the group of CTAs solving one system and this CTA's rank in it.
+__device__ __forceinline__ int grp_size(const Params& prm) {
+  return prm.group_ctas ? prm.group_ctas : (int)gridDim.x;
+}
+__device__ __forceinline__ int grp_rank(const Params& prm) {
+  return prm.group_ctas ? prm.group_rank : (int)blockIdx.x;
+}
+
 __device__ int grid_arrive(const Params& prm, SyncShared* ss) {
   __syncthreads();
+  if (prm.expected_ctas == 1u) {
+    // a group of one CTA: the CTA barrier is the whole synchronisation
+    if (threadIdx.x == 0) ss->flag = 1;
+    __syncthreads();
+    return 1;
+  }
   if (threadIdx.x == 0) {
     DevState* st = prm.st;
     __threadfence();
@@ -156,6 +170,7 @@ __device__ int grid_arrive(const Params& prm, SyncShared* ss) {
 
 __device__ void grid_release(const Params& prm, SyncShared* ss) {
   __syncthreads();
+  if (prm.expected_ctas == 1u) return;
   if (threadIdx.x == 0) {
     __threadfence();
     atomicExch(&prm.st->bar_count, 0u);
@@ -410,7 +425,7 @@ struct SerialSmem {
 // Compensated sum of a slot entry over the CTAs, in CTA order.
 __device__ __forceinline__ double sum_parts(const Params& prm, int off) {
   DSum t{0.0, 0.0};
-  const int G = gridDim.x;
+  const int G = grp_size(prm);
   for (int g = 0; g < G; ++g) {
     const double* q = prm.part + (size_t)g * kPartStride;
     dsum_add(t, ldcg(q + off), ldcg(q + kPartHalf + off));
@@ -780,13 +795,17 @@ struct LpShared {
   int m_seg;
   int m_any;
   int e_seg[4];             // per epilogue warp
+  int s_stage[2];           // per split warp (TF32x3)
+  unsigned s_phase[2];
   unsigned tmem;
   int issued[tc::kStages];  // phase of the last copy issued on each stage, -1 = none
 };
 
 template <int POL>
 struct LpCfg {
-  static constexpr int KIND = (POL == POL_FP8) ? tc::KIND_FP8 : tc::KIND_BF16;
+  static constexpr int KIND = (POL == POL_FP8)      ? tc::KIND_FP8
+                              : (POL == POL_TF32X3) ? tc::KIND_TF32X3
+                                                    : tc::KIND_BF16;
 };
 
 template <int P>
@@ -797,7 +816,8 @@ struct LpNP {
 template <int KIND, int NP>
 struct LpLayout {
   using S = tc::Shape<KIND, NP>;
-  static constexpr int kBars = 2 * tc::kStages + 5;  // full, empty, accf[2], acce[2], drain
+  // full[ST], empty[ST], split[ST], accf[2], acce[2], drain
+  static constexpr int kBars = 3 * S::kStagesK + 5;
   static constexpr size_t kBytes = 1024 + S::kRingBytes + kBars * 8 + sizeof(LpShared) + 64;
 };
 
@@ -819,6 +839,7 @@ __device__ void mbar_wait_drain(uint32_t a, uint32_t parity, long long timeout_n
 template <int KIND, int NP>
 __device__ void lp_pass(const Params& prm, LpCtx& L) {
   using S = tc::Shape<KIND, NP>;
+  constexpr int ST = S::kStagesK;
   constexpr uint32_t kIdesc = tc::idesc<KIND>(NP);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -829,10 +850,12 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
   const int64_t u0 = tc::unit_begin(U, G, c);
   const int64_t u1 = tc::unit_begin(U, G, c + 1);
   uint8_t* sA = L.ring;
-  uint8_t* sB = L.ring + tc::kStages * tc::kTileABytes;
+  uint8_t* sA2 = L.ring + ST * tc::kTileABytes;           // A_lo tiles (TF32x3)
+  uint8_t* sB = sA2 + ST * S::kTileA2Bytes;
   uint64_t* full = L.bars;
-  uint64_t* empty = L.bars + tc::kStages;
-  uint64_t* accf = L.bars + 2 * tc::kStages;
+  uint64_t* empty = L.bars + ST;
+  uint64_t* split = L.bars + 2 * ST;
+  uint64_t* accf = L.bars + 3 * ST;
   uint64_t* acce = accf + 2;
   int* err = &prm.st->error;
   const long long to = prm.timeout_ns;
@@ -854,7 +877,7 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
         tc::tma_load_2d(tc::smem_u32(sB + stage * S::kTileBBytes), &prm.lp_tmB,
                         k * prm.lp_kelems, 0, fb);
         L.sh->issued[stage] = (int)phase;
-        if (++stage == tc::kStages) { stage = 0; phase ^= 1u; }
+        if (++stage == ST) { stage = 0; phase ^= 1u; }
       }
       L.sh->p_stage = stage;
       L.sh->p_phase = phase;
@@ -874,17 +897,24 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
           if (!tc::mbar_wait(tc::smem_u32(&acce[b]), (((uint32_t)seg >> 1) & 1u) ^ 1u, to, err)) break;
           tc::fence_after();
         }
-        if (!tc::mbar_wait(tc::smem_u32(&full[stage]), phase, to, err)) break;
+        // TF32x3: the split warps signal once the tile has landed and its low
+        // part is written; the other kinds wait for the copy itself
+        uint64_t* ready = (KIND == tc::KIND_TF32X3) ? &split[stage] : &full[stage];
+        if (!tc::mbar_wait(tc::smem_u32(ready), phase, to, err)) break;
         tc::fence_after();
         const uint32_t dt = tmem + (uint32_t)(b * NP);
         const uint64_t ad = tc::sdesc(tc::smem_u32(sA + stage * tc::kTileABytes));
         const uint64_t bd = tc::sdesc(tc::smem_u32(sB + stage * S::kTileBBytes));
+        const uint64_t bl = tc::sdesc(tc::smem_u32(sB + stage * S::kTileBBytes + NP * tc::kRowBytes));
 #pragma unroll
         for (int kk = 0; kk < tc::kRowBytes / 32; ++kk) {
           tc::mma<KIND>(dt, ad + 2u * kk, bd + 2u * kk, kIdesc, (first && kk == 0) ? 0u : 1u);
-          if constexpr (KIND == tc::KIND_FP8) {
-            const uint64_t bl = tc::sdesc(tc::smem_u32(sB + stage * S::kTileBBytes + NP * tc::kRowBytes));
+          if constexpr (KIND != tc::KIND_BF16) {
             tc::mma<KIND>(dt, ad + 2u * kk, bl + 2u * kk, kIdesc, 1u);
+          }
+          if constexpr (KIND == tc::KIND_TF32X3) {
+            const uint64_t a2 = tc::sdesc(tc::smem_u32(sA2 + stage * tc::kTileABytes));
+            tc::mma<KIND>(dt, a2 + 2u * kk, bd + 2u * kk, kIdesc, 1u);
           }
         }
         L.sh->m_any = 1;
@@ -893,13 +923,45 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
           tc::mma_commit(tc::smem_u32(&accf[b]));
           ++seg;
         }
-        if (++stage == tc::kStages) { stage = 0; phase ^= 1u; }
+        if (++stage == ST) { stage = 0; phase ^= 1u; }
       }
       L.sh->m_stage = stage;
       L.sh->m_phase = phase;
       L.sh->m_seg = seg;
     }
-  } else if (warp >= 4) {
+  } else if (warp < 4) {
+    if constexpr (KIND == tc::KIND_TF32X3) {
+      // split warps: A_lo = A - tf32(A) for every landed FP32 tile, written at
+      // the same (swizzled) position of the A_lo ring
+      const int w = warp - 2;
+      const int t64 = threadIdx.x - 64;
+      int stage = L.sh->s_stage[w];
+      uint32_t phase = L.sh->s_phase[w];
+      for (int64_t u = u0; u < u1; ++u) {
+        if (!tc::mbar_wait(tc::smem_u32(&full[stage]), phase, to, err)) break;
+        const float4* src = reinterpret_cast<const float4*>(sA + stage * tc::kTileABytes);
+        float4* dst = reinterpret_cast<float4*>(sA2 + stage * tc::kTileABytes);
+        for (int v = t64; v < tc::kTileABytes / 16; v += 64) {
+          float4 a = src[v];
+          float4 lo;
+          lo.x = a.x - __uint_as_float(__float_as_uint(a.x) & 0xFFFFE000u);
+          lo.y = a.y - __uint_as_float(__float_as_uint(a.y) & 0xFFFFE000u);
+          lo.z = a.z - __uint_as_float(__float_as_uint(a.z) & 0xFFFFE000u);
+          lo.w = a.w - __uint_as_float(__float_as_uint(a.w) & 0xFFFFE000u);
+          dst[v] = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(tc::smem_u32(&split[stage]));
+        if (++stage == ST) { stage = 0; phase ^= 1u; }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        L.sh->s_stage[w] = stage;
+        L.sh->s_phase[w] = phase;
+      }
+    }
+  } else {
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
     int seg = L.sh->e_seg[quad];
@@ -962,6 +1024,13 @@ __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, 
     const double v = (j < pk) ? ldcg(V + i * p + j) : 0.0;
     if constexpr (KIND == tc::KIND_BF16) {
       reinterpret_cast<__nv_bfloat16*>(prm.lp_dq)[(int64_t)j * ldk + i] = __double2bfloat16(v);
+    } else if constexpr (KIND == tc::KIND_TF32X3) {
+      // hi = tf32(v) (low 13 mantissa bits cleared), lo = v - hi (exact in FP32)
+      const float f = (float)v;
+      const float hi = __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
+      float* o = reinterpret_cast<float*>(prm.lp_dq);
+      o[(int64_t)j * ldk + i] = hi;
+      o[(int64_t)(NP + j) * ldk + i] = f - hi;
     } else {
       const float sg = (j < pk) ? __ldcg(&st->sigma[j]) : 1.f;
       const double x = v / (double)sg;
@@ -1025,8 +1094,8 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
   __shared__ int s_err;
   SerialSmem& S = *reinterpret_cast<SerialSmem*>(smem);
   DevState* st = prm.st;
-  const int G = gridDim.x;
-  const int cta = blockIdx.x;
+  const int G = grp_size(prm);
+  const int cta = grp_rank(prm);
   const int tid = threadIdx.x;
   const int64_t n = prm.n;
   const int64_t r0 = ((int64_t)cta * n) / G;
@@ -1078,6 +1147,13 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       return;
     }
   } else {
+    if (prm.mode == MODE_BLOCK_PRODUCT) {
+      // W = A_lp V on the tensor cores (same code as the inner solves' A-pass)
+      if (lp_apass<P, POL>(prm, prm.V, prm.q, prm.Wout, false, r0, r1, *L, &ss, &s_err) &&
+          tid == 0 && cta == 0)
+        st->result = ST_OK;
+      return;
+    }
     if (prm.mode != MODE_SOLVE || !prm.skip_true_check) {
       if (tid == 0 && cta == 0) set_error(st, ST_ERR_INVALID, 14);
       return;
@@ -1290,16 +1366,18 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_kernel(const __grid_constant
     double* uni = reinterpret_cast<double*>(
         (reinterpret_cast<uintptr_t>(L.sh + 1) + 15) & ~uintptr_t(15));
     const int warp = threadIdx.x >> 5;
-    uint64_t* drain = L.bars + 2 * tc::kStages + 4;
+    constexpr int ST = S::kStagesK;
+    uint64_t* drain = L.bars + 3 * ST + 4;
     if (threadIdx.x == 0) {
-      for (int s = 0; s < tc::kStages; ++s) {
-        tc::mbar_init(tc::smem_u32(&L.bars[s]), 1);
-        tc::mbar_init(tc::smem_u32(&L.bars[tc::kStages + s]), 1);
-        L.sh->issued[s] = -1;
+      for (int s = 0; s < ST; ++s) {
+        tc::mbar_init(tc::smem_u32(&L.bars[s]), 1);           // full: TMA bytes
+        tc::mbar_init(tc::smem_u32(&L.bars[ST + s]), 1);      // empty: MMA commit
+        tc::mbar_init(tc::smem_u32(&L.bars[2 * ST + s]), 2);  // split: two warps
       }
+      for (int s = 0; s < tc::kStages; ++s) L.sh->issued[s] = -1;
       for (int b = 0; b < 2; ++b) {
-        tc::mbar_init(tc::smem_u32(&L.bars[2 * tc::kStages + b]), 1);
-        tc::mbar_init(tc::smem_u32(&L.bars[2 * tc::kStages + 2 + b]), 4);
+        tc::mbar_init(tc::smem_u32(&L.bars[3 * ST + b]), 1);
+        tc::mbar_init(tc::smem_u32(&L.bars[3 * ST + 2 + b]), 4);
       }
       tc::mbar_init(tc::smem_u32(drain), 1);
       L.sh->p_stage = 0;
@@ -1309,6 +1387,10 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_kernel(const __grid_constant
       L.sh->m_seg = 0;
       L.sh->m_any = 0;
       for (int q = 0; q < 4; ++q) L.sh->e_seg[q] = 0;
+      for (int q = 0; q < 2; ++q) {
+        L.sh->s_stage[q] = 0;
+        L.sh->s_phase[q] = 0;
+      }
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -1328,7 +1410,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_kernel(const __grid_constant
     // teardown: this CTA's copies and MMAs complete before TMEM is freed
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int s = 0; s < tc::kStages; ++s)
+      for (int s = 0; s < ST; ++s)
         if (L.sh->issued[s] >= 0)
           mbar_wait_drain(tc::smem_u32(&L.bars[s]), (uint32_t)L.sh->issued[s], prm.timeout_ns);
     }
@@ -1344,6 +1426,75 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_kernel(const __grid_constant
                    "r"(S::kTmemCols)
                    : "memory");
     }
+  }
+}
+
+// Batched solver: each CTA repeatedly takes the next system from the queue
+// (largest first, as ordered by the host) and solves it alone -- the solver
+// body with a group of one CTA, whose barriers are CTA barriers.
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1) batch_kernel(const __grid_constant__ Params prm) {
+  extern __shared__ __align__(1024) uint8_t dyn_smem[];
+  __shared__ Params q;
+  __shared__ long long s_sys;
+  const int tid = threadIdx.x;
+  const size_t slot = blockIdx.x;
+  for (;;) {
+    if (tid == 0) s_sys = (long long)atomicAdd(prm.batch_next, 1u);
+    __syncthreads();
+    const long long i = s_sys;
+    if (i >= prm.batch_count) break;
+    if (tid == 0) {
+      const int64_t* d = prm.batch_desc + 4 * i;  // n, A offset, vector offset, index
+      q = prm;
+      q.n = d[0];
+      q.lda = d[0] + (d[0] & 1);
+      q.A = prm.A + d[1];
+      q.b = prm.b + d[2];
+      q.x_out = prm.x_out + d[2];
+      double* w = prm.X + slot * (size_t)prm.batch_slot_stride;
+      const size_t blk = (size_t)prm.batch_slot_stride / 5;
+      q.X = w;
+      q.R = w + blk;
+      q.D0 = w + 2 * blk;
+      q.D1 = w + 3 * blk;
+      q.W = w + 4 * blk;
+      q.part = prm.part + slot * kPartStride;
+      q.st = prm.st + slot;
+      q.expected_ctas = 1u;
+      q.group_ctas = 1;
+      q.group_rank = 0;
+      DevState* st = q.st;
+      st->bar_count = 0;
+      st->bar_gen = 0;
+      st->error = 0;
+      st->result = 0;
+      st->ctrl = 0;
+      st->k = 0;
+      st->pk = prm.p;
+      st->prev_pk = prm.p;
+      st->changed = 0;
+      st->jbest = 0;
+      st->replacements = 0;
+      st->drops = 0;
+      st->k_replaced = -1;
+      st->zero_rhs = 0;
+      st->relres_true = 0.0;
+      for (int j = 0; j < kMaxP; ++j) st->agent[j] = j;
+      __threadfence();
+    }
+    __syncthreads();
+    solve_body<P, false, POL_FP64>(q, reinterpret_cast<double*>(dyn_smem), nullptr);
+    __syncthreads();
+    if (tid == 0) {
+      const DevState* st = q.st;
+      const int64_t idx = prm.batch_desc[4 * i + 3];
+      const int err = *(volatile const int*)&st->error;
+      prm.batch_status[idx] = err != 0 ? err : *(volatile const int*)&st->result;
+      prm.batch_iters[idx] = *(volatile const int*)&st->k;
+      prm.batch_relres[idx] = *(volatile const double*)&st->relres_true;
+    }
+    __syncthreads();
   }
 }
 

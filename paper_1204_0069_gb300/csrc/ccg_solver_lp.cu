@@ -8,28 +8,49 @@
 
 namespace ccg {
 
-void* select_kernel_lp(int P, int pol) {
-  const bool fp8 = pol == POL_FP8;
+namespace {
+
+template <int POL>
+void* select_pol(int P) {
   switch (P) {
-    case 1: return fp8 ? kernel_ptr<1, true, POL_FP8>() : kernel_ptr<1, true, POL_BF16>();
-    case 2: return fp8 ? kernel_ptr<2, true, POL_FP8>() : kernel_ptr<2, true, POL_BF16>();
-    case 4: return fp8 ? kernel_ptr<4, true, POL_FP8>() : kernel_ptr<4, true, POL_BF16>();
-    case 8: return fp8 ? kernel_ptr<8, true, POL_FP8>() : kernel_ptr<8, true, POL_BF16>();
-    case 16: return fp8 ? kernel_ptr<16, true, POL_FP8>() : kernel_ptr<16, true, POL_BF16>();
-    case 32: return fp8 ? kernel_ptr<32, true, POL_FP8>() : kernel_ptr<32, true, POL_BF16>();
+    case 1: return kernel_ptr<1, true, POL>();
+    case 2: return kernel_ptr<2, true, POL>();
+    case 4: return kernel_ptr<4, true, POL>();
+    case 8: return kernel_ptr<8, true, POL>();
+    case 16: return kernel_ptr<16, true, POL>();
+    case 32: return kernel_ptr<32, true, POL>();
+    default: return nullptr;
+  }
+}
+
+template <int POL>
+size_t smem_pol(int P) {
+  switch (P) {
+    case 1: return solver_smem_bytes<1, POL>();
+    case 2: return solver_smem_bytes<2, POL>();
+    case 4: return solver_smem_bytes<4, POL>();
+    case 8: return solver_smem_bytes<8, POL>();
+    case 16: return solver_smem_bytes<16, POL>();
+    default: return solver_smem_bytes<32, POL>();
+  }
+}
+
+}  // namespace
+
+void* select_kernel_lp(int P, int pol) {
+  switch (pol) {
+    case POL_BF16: return select_pol<POL_BF16>(P);
+    case POL_FP8: return select_pol<POL_FP8>(P);
+    case POL_TF32X3: return select_pol<POL_TF32X3>(P);
     default: return nullptr;
   }
 }
 
 size_t solver_smem_bytes_lp(int P, int pol) {
-  const bool fp8 = pol == POL_FP8;
-  switch (P) {
-    case 1: return fp8 ? solver_smem_bytes<1, POL_FP8>() : solver_smem_bytes<1, POL_BF16>();
-    case 2: return fp8 ? solver_smem_bytes<2, POL_FP8>() : solver_smem_bytes<2, POL_BF16>();
-    case 4: return fp8 ? solver_smem_bytes<4, POL_FP8>() : solver_smem_bytes<4, POL_BF16>();
-    case 8: return fp8 ? solver_smem_bytes<8, POL_FP8>() : solver_smem_bytes<8, POL_BF16>();
-    case 16: return fp8 ? solver_smem_bytes<16, POL_FP8>() : solver_smem_bytes<16, POL_BF16>();
-    default: return fp8 ? solver_smem_bytes<32, POL_FP8>() : solver_smem_bytes<32, POL_BF16>();
+  switch (pol) {
+    case POL_BF16: return smem_pol<POL_BF16>(P);
+    case POL_FP8: return smem_pol<POL_FP8>(P);
+    default: return smem_pol<POL_TF32X3>(P);
   }
 }
 

@@ -13,20 +13,26 @@
 namespace ccg {
 namespace tc {
 
-enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1 };
+// Kinds of quantised A: BF16; FP8 E4M3 with row scales (operand as two E4M3
+// terms); FP32 multiplied as three TF32 products (A_hi D_hi + A_hi D_lo +
+// A_lo D_hi, the low parts split off in shared memory / at conversion).
+enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1, KIND_TF32X3 = 2 };
 
 constexpr int kBM = 128;          // rows per tile (MMA M)
 constexpr int kRowBytes = 128;    // K bytes per stage = one 128-byte swizzle atom
-constexpr int kStages = 6;
+constexpr int kStages = 6;        // ring depth of the BF16 / FP8 kinds
 constexpr int kTileABytes = kBM * kRowBytes;  // 16 KB
 
 template <int KIND, int NP>
 struct Shape {
-  static constexpr int NB = (KIND == KIND_FP8) ? 2 * NP : NP;  // B rows per stage
+  static constexpr int NB = (KIND == KIND_BF16) ? NP : 2 * NP;   // B rows (hi, lo)
+  static constexpr int kStagesK = (KIND == KIND_TF32X3) ? 4 : kStages;
   static constexpr int kTileBBytes = NB * kRowBytes;
-  static constexpr int kStageBytes = kTileABytes + kTileBBytes;
+  static constexpr int kTileA2Bytes = (KIND == KIND_TF32X3) ? kTileABytes : 0;  // A_lo
+  static constexpr int kStageBytes = kTileABytes + kTileBBytes;  // bytes one TMA stage brings
   static constexpr int kTmemCols = (2 * NP < 32) ? 32 : 2 * NP;  // two accumulators
-  static constexpr int kRingBytes = kStages * kStageBytes;
+  static constexpr int kRingBytes = kStagesK * (kTileABytes + kTileA2Bytes + kTileBBytes);
+  static constexpr int kElemBytes = (KIND == KIND_BF16) ? 2 : (KIND == KIND_FP8) ? 1 : 4;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -98,7 +104,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
                                     uint32_t accum) {
-  if constexpr (KIND == KIND_BF16) {
+  if constexpr (KIND == KIND_TF32X3) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+        : "memory");
+  } else if constexpr (KIND == KIND_BF16) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
@@ -128,8 +140,8 @@ __device__ __forceinline__ void fence_before() {
 template <int KIND>
 __host__ __device__ constexpr uint32_t idesc(int N) {
   return (1u << 4)                                  // D format F32
-         | ((KIND == KIND_BF16 ? 1u : 0u) << 7)     // A format: BF16 / E4M3
-         | ((KIND == KIND_BF16 ? 1u : 0u) << 10)    // B format: BF16 / E4M3
+         | ((KIND == KIND_BF16 ? 1u : KIND == KIND_TF32X3 ? 2u : 0u) << 7)   // A: BF16 / TF32 / E4M3
+         | ((KIND == KIND_BF16 ? 1u : KIND == KIND_TF32X3 ? 2u : 0u) << 10)  // B: same
          | ((uint32_t)(N >> 3) << 17)               // N / 8
          | ((uint32_t)(kBM >> 4) << 24);            // M / 16
 }

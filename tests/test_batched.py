@@ -1,0 +1,80 @@
+"""GPU tests of the batched solver: many independent SPD systems of uneven
+size in one persistent launch (one CTA per system at a time, largest first).
+Every system is checked against the FP64 oracle with the parity bar of the
+single-system solver (relres <= 1e-10, ||x - x_oracle|| / ||x_oracle|| <=
+1e-8, iterations within 2)."""
+import numpy as np
+import pytest
+
+from paper_1204_0069_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1204_0069_gb300 import build as B
+    B.build()
+    import oracle
+    oracle.build()
+    from paper_1204_0069_gb300 import ccg
+    return dict(torch=torch, ccg=ccg, oracle=oracle)
+
+
+def make_batch(sizes, seed):
+    rng = np.random.default_rng(seed)
+    mats, rhs = [], []
+    for k, n in enumerate(sizes):
+        A, b = wl.gram_shift(int(n), seed=seed * 100003 + k, shift=float(rng.uniform(0.05, 1.0)))
+        mats.append(A)
+        rhs.append(b)
+    return mats, rhs
+
+
+def pack(ccg, torch, sizes, mats, rhs):
+    a_off, v_off, at, vt = ccg.batch_offsets(sizes)
+    Ap = np.zeros(at)
+    bp = np.zeros(vt)
+    for n, A, b, ao, vo in zip(sizes, mats, rhs, a_off, v_off):
+        ld = n + (n & 1)
+        Ap[ao:ao + n * ld].reshape(n, ld)[:, :n] = A
+        bp[vo:vo + n] = b
+    return torch.from_numpy(Ap).cuda(), torch.from_numpy(bp).cuda(), v_off
+
+
+@pytest.mark.parametrize("p", [1, 4, 7])
+def test_batched_matches_oracle_per_system(env, p):
+    torch, ccg, oracle = env["torch"], env["ccg"], env["oracle"]
+    rng = np.random.default_rng(p)
+    sizes = [int(v) for v in np.round(np.exp(rng.uniform(np.log(8), np.log(300), 150)))]
+    sizes = [max(s, p) for s in sizes] + [p, 301, 17]
+    mats, rhs = make_batch(sizes, seed=p)
+    dA, db, v_off = pack(ccg, torch, sizes, mats, rhs)
+    x = torch.zeros_like(db)
+    with ccg.Solver() as s:
+        summ, st, it, rr = s.solve_batched(sizes, dA, db, x, p=p, tol=1e-10, maxit=10000)
+    assert summ.status == 0, summ
+    xs = x.cpu().numpy()
+    for k, (n, A, b) in enumerate(zip(sizes, mats, rhs)):
+        xi = xs[v_off[k]:v_off[k] + n]
+        assert st[k] == 0
+        relres = np.linalg.norm(b - A @ xi) / np.linalg.norm(b)
+        assert relres <= 1.01e-10 and rr[k] <= 1e-10
+        X0 = oracle.initial_block(n, p, None, 1.0, 0)
+        ref = oracle.ccg(A, b, X0, 1e-10, 10000)
+        err = np.linalg.norm(xi - ref["x"]) / np.linalg.norm(ref["x"])
+        assert err <= 1e-8, (k, n, err)
+        assert abs(int(it[k]) - ref["iterations"]) <= 2, (k, n, it[k], ref["iterations"])
+
+
+def test_batched_empty_and_invalid(env):
+    torch, ccg = env["torch"], env["ccg"]
+    with ccg.Solver() as s:
+        z = torch.zeros(4, dtype=torch.float64, device="cuda")
+        summ, *_ = s.solve_batched([], z, z, z, p=2, tol=1e-8, maxit=10)
+        assert summ.status == 0
+        summ, *_ = s.solve_batched([1], z, z, z, p=2, tol=1e-8, maxit=10)  # p > n
+        assert summ.status == -1

@@ -58,7 +58,25 @@ def e4m3_round(torch, x):
     return round_to_format(x, 4, min_exp=-6, max_abs=448.0)
 
 
+def tf32_trunc(x32):
+    """TF32 part of FP32 values: the low 13 mantissa bits cleared."""
+    b = np.ascontiguousarray(x32, dtype=np.float32).view(np.uint32) & np.uint32(0xFFFFE000)
+    return b.view(np.float32).astype(np.float64)
+
+
 def reference(torch, A, V, fmt):
+    if fmt == 2:
+        # FP32 A; three TF32 products A_hi D_hi + A_hi D_lo + A_lo D_hi with
+        # hi = tf32(x), lo = tf32(x - hi) (x rounded to FP32 first)
+        Af = A.astype(np.float32)
+        Ah = tf32_trunc(Af)
+        Al = tf32_trunc((Af.astype(np.float64) - Ah).astype(np.float32))
+        Vf = V.astype(np.float32)
+        Vh = tf32_trunc(Vf)
+        Vl = tf32_trunc((Vf.astype(np.float64) - Vh).astype(np.float32))
+        W = Ah @ Vh + Ah @ Vl + Al @ Vh
+        mag = np.abs(Ah) @ np.abs(Vh) + np.abs(Ah) @ np.abs(Vl) + np.abs(Al) @ np.abs(Vh)
+        return W, mag
     if fmt == 0:
         Aq = bf16_round(torch, A)
         Vq = bf16_round(torch, V)
@@ -75,7 +93,7 @@ def reference(torch, A, V, fmt):
     return Aq @ Vq, np.abs(Aq) @ np.abs(Vq)
 
 
-@pytest.mark.parametrize("fmt", [0, 1], ids=["bf16", "fp8"])
+@pytest.mark.parametrize("fmt", [0, 1, 2], ids=["bf16", "fp8", "fp32_tf32x3"])
 @pytest.mark.parametrize("n,q", CASES)
 def test_lowp_block_product(env, fmt, n, q):
     torch = env["torch"]
@@ -90,7 +108,15 @@ def test_lowp_block_product(env, fmt, n, q):
     assert rc == 0
     ref, mag = reference(torch, A, V, fmt)
     err = np.abs(W.cpu().numpy() - ref)
-    bound = 2.0 * (n / 16 + 8) * 2.0 ** -24 * mag
+    if fmt == 2:
+        # 3 MMAs per 8 k (K = 8 per TF32 MMA); plus the TF32 reading of the low
+        # parts (truncation or rounding: one TF32 ulp of a low part)
+        bound = 2.0 * (3 * n / 8 + 8) * 2.0 ** -24 * mag + 2.0 ** -19 * mag
+        # and the product is FP32-accurate against the exact FP64 one
+        exact = np.abs(W.cpu().numpy() - A @ V)
+        assert np.all(exact <= 2.0 ** -16 * (np.abs(A) @ np.abs(V)))
+    else:
+        bound = 2.0 * (n / 16 + 8) * 2.0 ** -24 * mag
     assert np.all(err <= bound + 1e-300), (err / mag).max()
     # repeated call on the same operands is bitwise identical (fixed-order fixup)
     W2 = torch.zeros_like(W)

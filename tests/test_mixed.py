@@ -58,6 +58,22 @@ def test_mixed_reaches_fp64_accuracy(env, precision, shift, n, p):
     assert r.outer_steps >= 2 and r.iterations > 0
 
 
+@pytest.mark.parametrize("n,p", [(2048, 8), (1500, 4), (3000, 16)])
+def test_fp32_ir_reaches_fp64_on_ill_conditioned_kernel(env, n, p):
+    """Exponential kernel (kappa ~ 1e4): A stored in FP32 with TF32x3 tensor-core
+    products is accurate enough (kappa * 2^-21 << 1) for refinement to reach
+    the FP64 target."""
+    A, b = wl.exp_kernel(n, seed=1, length=0.2, nugget=1e-2)
+    r, x = solve(env, A, b, p, 1)
+    assert r.status == 0, r
+    relres = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    assert relres <= 1e-10 * 1.01, relres
+    X0 = env["oracle"].initial_block(n, p, None, 1.0, 0)
+    ref = env["oracle"].ccg(A, b, X0, 1e-10, 20 * n, nthreads=8)
+    err = np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"])
+    assert err <= 1e-8, err
+
+
 def test_mixed_reports_truthfully_when_refinement_stalls(env):
     """Exponential kernel, kappa ~ 1e4: BF16 A is too coarse for plain
     refinement to reach 1e-10; the status and residual must say so."""

@@ -1,0 +1,86 @@
+"""GPU tests of the serving loop: continuous admission of solve requests.
+
+* every result equals the same request solved alone (same worker share,
+  hence the same grid): bitwise, which is within any stated tolerance;
+* requests admitted while others run overlap (peak in-flight > 1);
+* the device-memory budget is never exceeded and a request larger than the
+  budget is refused at submission.
+"""
+import numpy as np
+import pytest
+
+from paper_1204_0069_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1204_0069_gb300 import build as B
+    B.build()
+    from paper_1204_0069_gb300 import ccg
+    return dict(torch=torch, ccg=ccg)
+
+
+def requests(torch, count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(np.round(np.exp(rng.uniform(np.log(200), np.log(2500)))))
+        A, b = wl.exp_kernel(n, seed=seed * 1000 + k, length=float(rng.uniform(0.05, 0.5)),
+                             nugget=float(10 ** rng.uniform(-4, -1)))
+        tol = [1e-6, 1e-10][k % 2]
+        out.append((torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), tol, A, b))
+    return out
+
+
+def run_server(ccg, torch, reqs, workers, budget, precision=0, share=16):
+    srv = ccg.Server(workers=workers, budget_bytes=budget, precision=precision,
+                     ctas_per_worker=share)
+    xs = [torch.zeros(b.shape[0], dtype=torch.float64, device="cuda") for _, b, *_ in reqs]
+    for k, (A, b, tol, *_) in enumerate(reqs):
+        assert srv.submit(k, A, b, xs[k], p=8, tol=tol, maxit=50000) == 0
+    got = {}
+    while len(got) < len(reqs):
+        for r in srv.poll(64, wait_ms=200):
+            got[r["id"]] = r
+    st = srv.stats()
+    srv.close()
+    return got, [x.cpu().numpy() for x in xs], st
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32_ir"])
+def test_results_alone_equal_results_in_the_mix(env, precision):
+    torch, ccg = env["torch"], env["ccg"]
+    reqs = requests(torch, 10, seed=5)
+    mix, xmix, st = run_server(ccg, torch, reqs, workers=6, budget=150e9, precision=precision)
+    assert st["peak_in_flight"] > 1
+    for k, (A, b, tol, An, bn) in enumerate(reqs):
+        r = mix[k]
+        assert r["status"] == 0, r
+        relres = np.linalg.norm(bn - An @ xmix[k]) / np.linalg.norm(bn)
+        assert relres <= tol * 1.01
+        alone, xal, _ = run_server(ccg, torch, [reqs[k]], workers=1, budget=150e9,
+                                   precision=precision)
+        assert alone[0]["iterations"] == r["iterations"]
+        assert np.array_equal(xal[0], xmix[k])
+
+
+def test_budget_is_respected(env):
+    torch, ccg = env["torch"], env["ccg"]
+    reqs = requests(torch, 8, seed=9)
+    biggest = max(int(b.shape[0]) for _, b, *_ in reqs)
+    budget = 2.5 * biggest * biggest * 8 + 64e6  # room for about two of the largest
+    got, xs, st = run_server(ccg, torch, reqs, workers=6, budget=budget)
+    assert st["peak_reserved_bytes"] <= budget
+    assert all(r["status"] == 0 for r in got.values())
+    # admission waits for memory: some request was admitted after it was queued
+    assert any(r["admit_ms"] - r["submit_ms"] > 0.0 for r in got.values())
+    srv = ccg.Server(workers=1, budget_bytes=1e6)
+    A, b, *_ = reqs[0]
+    x = torch.zeros_like(b)
+    assert srv.submit(0, A, b, x, p=4, tol=1e-8, maxit=100) == -4  # can never fit
+    srv.close()
