@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--maxit", type=int, default=0, help="iteration cap (0 = 20 n)")
-    ap.add_argument("--profile", default="none", choices=["none", "solve", "block", "lowp"],
+    ap.add_argument("--profile", default="none",
+                    choices=["none", "solve", "block", "lowp", "mixed", "lowp32"],
                     help="profiling driver: run only K solves, K FP64 block products or K "
                          "tensor-core block products (n = 32768)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision lines")
@@ -392,6 +393,27 @@ def main():
     solver = ccg.Solver(device=local, stream=stream.cuda_stream)
     maxit = args.maxit if args.maxit > 0 else 20 * n
 
+    if args.profile == "mixed":
+        # mixed-precision (FP32_IR) solves of the benchmark system
+        with ccg.Solver(stream=stream.cuda_stream, precision=ccg.FP32_IR) as sm:
+            for _ in range(args.warmup + args.steps):
+                r = sm.solve(dA, db, x, p=p, tol=TOL, maxit=maxit)
+                print(json.dumps({"status": r.status_name, "iterations": r.iterations,
+                                  "outer": r.outer_steps, "ms": r.device_ms}), flush=True)
+        solver.close()
+        return
+    if args.profile == "lowp32":
+        # FP32 (TF32x3) block products of the benchmark matrix through the
+        # persistent kernel's tensor-core A-pass
+        m = solver.lowp_matrix(dA, ccg.LOWP_FP32)
+        V = torch.randn(n, p, dtype=torch.float64, device=dev)
+        W = torch.empty(n, p, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup + args.steps):
+            rc, ms = m.block_product(V, W)
+            print(json.dumps({"rc": rc, "ms": ms}), flush=True)
+        m.close()
+        solver.close()
+        return
     if args.profile == "lowp":
         A32 = device_exp_kernel(args.lowp_n, 2, 0.1, 1e-3, dev)
         m = solver.lowp_matrix(A32, ccg.LOWP_BF16)

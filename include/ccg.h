@@ -57,7 +57,7 @@ typedef enum {
 
 typedef enum {
     CCG_FP64 = 0,            /* every operation in FP64                      */
-    CCG_FP32_IR = 1,         /* A in FP32, products as three TF32 terms on the
+    CCG_FP32_IR = 1,         /* A in FP32, products from TF32 halves on the
                                 tensor cores, FP64 refinement                 */
     CCG_BF16_IR = 2,         /* A in BF16 on the tensor cores, FP64 refinement */
     CCG_FP8_IR = 3           /* A in FP8 E4M3 on the tensor cores, FP64 refinement */
@@ -173,9 +173,9 @@ typedef enum {
     CCG_LOWP_FP8_E4M3 = 1,  /* FP8 E4M3, one FP32 scale per row: A_ij ~= s_i q_ij,
                                s_i = max_j |A_ij| / 448 (1 byte/entry)        */
     CCG_LOWP_FP32 = 2       /* FP32 (4 bytes/entry); the tensor cores form
-                               A_hi D_hi + A_hi D_lo + A_lo D_hi with TF32
-                               halves (A_lo = A - tf32(A)), about 2^-21
-                               relative error per product                     */
+                               (A_hi + A_lo)(D_hi + D_lo) from TF32 halves
+                               (A_lo = A - tf32(A)), about 2^-21 relative
+                               error per product                              */
 } ccg_lowp_format;
 
 /* Opaque quantised matrix (device memory owned by the object). */

@@ -147,8 +147,8 @@ struct Params {
   double ref_coef;
   double* ref_r;           // A x - b
   double* ref_bin;         // -(A x - b) * sqrt(n) / ||b - A x||
-  alignas(64) CUtensorMap lp_tmA;  // A_lp tiles
-  alignas(64) CUtensorMap lp_tmB;  // operand tiles
+  CUtensorMap lp_tmA;  // A_lp tiles (the type carries its alignment)
+  CUtensorMap lp_tmB;  // operand tiles
 };
 
 // Launch helpers implemented in ccg_fp64.cu.

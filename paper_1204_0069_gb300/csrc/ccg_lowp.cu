@@ -49,8 +49,9 @@ __global__ void __launch_bounds__(kThreadsLp, 1)
   constexpr int NB = (KIND == KIND_FP8) ? 2 * NP : NP;  // B rows per stage (hi + lo for FP8)
   constexpr int kTileBBytes = NB * kRowBytes;
   constexpr int kStageBytes = kTileABytes + kTileBBytes;
-  constexpr uint32_t kIdesc = idesc<KIND>(NP);
-  constexpr int kTmemCols = (2 * NP < 32) ? 32 : 2 * NP;  // two accumulator buffers
+  constexpr int NM = NB;  // one MMA covers hi and lo rows; the epilogue adds the halves
+  constexpr uint32_t kIdesc = idesc<KIND>(NM);
+  constexpr int kTmemCols = (2 * NM < 32) ? 32 : 2 * NM;  // two accumulator buffers
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment for the swizzled tiles
@@ -149,17 +150,13 @@ __global__ void __launch_bounds__(kThreadsLp, 1)
         ok = mbar_wait(smem_u32(&full[stage]), phase, run.timeout_ns, err);
         if (!ok) break;
         fence_after();
-        const uint32_t dt = tmem + (uint32_t)(b * NP);
+        const uint32_t dt = tmem + (uint32_t)(b * NM);
         const uint64_t ad = sdesc(smem_u32(sA + stage * kTileABytes));
         const uint64_t bd = sdesc(smem_u32(sB + stage * kTileBBytes));
 #pragma unroll
         for (int kk = 0; kk < kRowBytes / 32; ++kk) {
           // advance 32 bytes along K inside the swizzle atom
           mma<KIND>(dt, ad + 2u * kk, bd + 2u * kk, kIdesc, (first && kk == 0) ? 0u : 1u);
-          if constexpr (KIND == KIND_FP8) {
-            const uint64_t bl = sdesc(smem_u32(sB + stage * kTileBBytes + NP * kRowBytes));
-            mma<KIND>(dt, ad + 2u * kk, bl + 2u * kk, kIdesc, 1u);
-          }
         }
         issued_any = true;
         mma_commit(smem_u32(&empty[stage]));
@@ -187,8 +184,12 @@ __global__ void __launch_bounds__(kThreadsLp, 1)
         const int b = seg & 1;
         if (!mbar_wait(smem_u32(&accf[b]), ((uint32_t)seg >> 1) & 1u, run.timeout_ns, err)) break;
         fence_after();
-        float v[NP];
-        tmem_ld<NP>(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * NP), v);
+        float v[NM];
+        tmem_ld<NM>(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * NM), v);
+        if constexpr (NM != NP) {
+#pragma unroll
+          for (int j = 0; j < NP; ++j) v[j] += v[NP + j];  // hi + lo halves
+        }
         float* dst = run.part + ((size_t)(c + t) * kBM + row) * NP;
 #pragma unroll
         for (int j = 0; j < NP; j += 4)

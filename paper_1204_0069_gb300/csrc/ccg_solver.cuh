@@ -280,12 +280,82 @@ __device__ __forceinline__ void load_a_chunk(const double* Arow, int64_t n, int6
   }
 }
 
+// Narrow block product (P <= 2 operand columns, which fit in L1): every warp
+// streams its own rows with 8 independent 16-byte loads in flight per lane and
+// reads the operand through L1; no CTA barrier per k-chunk.  The operand was
+// written before the last grid barrier, whose acquire makes L1 reads fresh.
+template <int P, bool VEC>
+__device__ void apass_narrow(const Params& prm, const double* __restrict__ V, int ldv,
+                             int coff, int pk, double* __restrict__ Y, int ldy,
+                             bool sub_b, int64_t r0, int64_t r1) {
+  constexpr int U = 8;                  // double2 loads of A per lane per step
+  constexpr int NS = 4;                 // accumulator sets
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t n = prm.n;
+  const int64_t lda = prm.lda;
+  const int64_t nr = r1 - r0;
+  const int64_t w0 = r0 + (nr * warp) / kWarps;
+  const int64_t w1 = r0 + (nr * (warp + 1)) / kWarps;
+  for (int64_t row = w0; row < w1; ++row) {
+    const double* Arow = prm.A + row * lda;
+    double acc[NS][P];
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int c = 0; c < P; ++c) acc[s][c] = 0.0;
+    for (int64_t k0 = 0; k0 < n; k0 += 64 * U) {
+      double2 a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = k0 + 64 * u + 2 * lane;
+        double2 t = make_double2(0.0, 0.0);
+        if (VEC && k + 1 < n) {
+          t = __ldcs(reinterpret_cast<const double2*>(Arow + k));
+        } else {
+          if (k < n) t.x = __ldcs(Arow + k);
+          if (k + 1 < n) t.y = __ldcs(Arow + k + 1);
+        }
+        a[u] = t;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = k0 + 64 * u + 2 * lane;
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+          const bool in0 = c < pk && k < n, in1 = c < pk && k + 1 < n;
+          const double vx = in0 ? __ldca(V + k * ldv + coff + c) : 0.0;
+          const double vy = in1 ? __ldca(V + (k + 1) * ldv + coff + c) : 0.0;
+          acc[(2 * u) % NS][c] = fma(a[u].x, vx, acc[(2 * u) % NS][c]);
+          acc[(2 * u + 1) % NS][c] = fma(a[u].y, vy, acc[(2 * u + 1) % NS][c]);
+        }
+      }
+    }
+    double tot[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) tot[c] = (acc[0][c] + acc[1][c]) + (acc[2][c] + acc[3][c]);
+    ReduceScatter<P, 16>::run(tot, lane);
+    const int c = lane >> (5 - Tile<P>::LOGP);
+    const bool owner = (lane & ((32 >> Tile<P>::LOGP) - 1)) == 0;
+    if (owner && c < pk) {
+      double y = tot[0];
+      if (sub_b) y -= prm.b[row];
+      Y[row * ldy + c] = y;
+    }
+  }
+  __syncthreads();
+}
+
 // Y[row, c] = sum_k A[row, k] V[k, coff + c] (- b[row]) for the rows
 // [r0, r1) and c < pk.  Vs: shared scratch of 2 * P * VSTR doubles.
 template <int P, bool VEC>
 __device__ void apass(const Params& prm, const double* __restrict__ V, int ldv,
                       int coff, int pk, double* __restrict__ Y, int ldy,
                       bool sub_b, int64_t r0, int64_t r1, double* Vs) {
+  if constexpr (P <= 2) {
+    apass_narrow<P, VEC>(prm, V, ldv, coff, pk, Y, ldy, sub_b, r0, r1);
+    return;
+  }
   using T = Tile<P>;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -383,7 +453,20 @@ __device__ void partial_grams(const double* U0, const double* V0, const double* 
     }
     if (U == nullptr) continue;
     DSum t{0.0, 0.0};
-    for (int64_t i = r0; i < r1; ++i) dsum_fma(t, ldcg(U + i * ld + a), ldcg(Vv + i * ld + c));
+    int64_t i = r0;
+    // blocks of 8 rows: 16 independent loads in flight, then the compensated
+    // sum in row order (the same order as one row at a time)
+    for (; i + 8 <= r1; i += 8) {
+      double u[8], v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        u[q] = ldcg(U + (i + q) * ld + a);
+        v[q] = ldcg(Vv + (i + q) * ld + c);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dsum_fma(t, u[q], v[q]);
+    }
+    for (; i < r1; ++i) dsum_fma(t, ldcg(U + i * ld + a), ldcg(Vv + i * ld + c));
     out[slot] = t.hi;
     out[kPartHalf + slot] = t.lo;
   }
@@ -426,7 +509,20 @@ struct SerialSmem {
 __device__ __forceinline__ double sum_parts(const Params& prm, int off) {
   DSum t{0.0, 0.0};
   const int G = grp_size(prm);
-  for (int g = 0; g < G; ++g) {
+  int g = 0;
+  // blocks of 8 CTAs: 16 independent loads in flight, summed in CTA order
+  for (; g + 8 <= G; g += 8) {
+    double h[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double* pp = prm.part + (size_t)(g + q) * kPartStride;
+      h[q] = ldcg(pp + off);
+      l[q] = ldcg(pp + kPartHalf + off);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dsum_add(t, h[q], l[q]);
+  }
+  for (; g < G; ++g) {
     const double* q = prm.part + (size_t)g * kPartStride;
     dsum_add(t, ldcg(q + off), ldcg(q + kPartHalf + off));
   }
@@ -840,7 +936,8 @@ template <int KIND, int NP>
 __device__ void lp_pass(const Params& prm, LpCtx& L) {
   using S = tc::Shape<KIND, NP>;
   constexpr int ST = S::kStagesK;
-  constexpr uint32_t kIdesc = tc::idesc<KIND>(NP);
+  constexpr int NM = S::NMMA;
+  constexpr uint32_t kIdesc = tc::idesc<KIND>(NM);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
@@ -902,16 +999,13 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
         uint64_t* ready = (KIND == tc::KIND_TF32X3) ? &split[stage] : &full[stage];
         if (!tc::mbar_wait(tc::smem_u32(ready), phase, to, err)) break;
         tc::fence_after();
-        const uint32_t dt = tmem + (uint32_t)(b * NP);
+        const uint32_t dt = tmem + (uint32_t)(b * NM);
         const uint64_t ad = tc::sdesc(tc::smem_u32(sA + stage * tc::kTileABytes));
         const uint64_t bd = tc::sdesc(tc::smem_u32(sB + stage * S::kTileBBytes));
-        const uint64_t bl = tc::sdesc(tc::smem_u32(sB + stage * S::kTileBBytes + NP * tc::kRowBytes));
 #pragma unroll
         for (int kk = 0; kk < tc::kRowBytes / 32; ++kk) {
+          // N = NM covers the operand's hi and lo rows (FP8, TF32x3)
           tc::mma<KIND>(dt, ad + 2u * kk, bd + 2u * kk, kIdesc, (first && kk == 0) ? 0u : 1u);
-          if constexpr (KIND != tc::KIND_BF16) {
-            tc::mma<KIND>(dt, ad + 2u * kk, bl + 2u * kk, kIdesc, 1u);
-          }
           if constexpr (KIND == tc::KIND_TF32X3) {
             const uint64_t a2 = tc::sdesc(tc::smem_u32(sA2 + stage * tc::kTileABytes));
             tc::mma<KIND>(dt, a2 + 2u * kk, bd + 2u * kk, kIdesc, 1u);
@@ -972,8 +1066,12 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
         const int b = seg & 1;
         if (!tc::mbar_wait(tc::smem_u32(&accf[b]), ((uint32_t)seg >> 1) & 1u, to, err)) break;
         tc::fence_after();
-        float v[NP];
-        tc::tmem_ld<NP>(L.sh->tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * NP), v);
+        float v[NM];
+        tc::tmem_ld<NM>(L.sh->tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * NM), v);
+        if constexpr (NM != NP) {
+#pragma unroll
+          for (int j = 0; j < NP; ++j) v[j] += v[NP + j];  // hi + lo halves
+        }
         float* dst = prm.lp_part + ((size_t)(c + t) * tc::kBM + row) * NP;
 #pragma unroll
         for (int j = 0; j < NP; j += 4)
@@ -1308,6 +1406,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         const int64_t i = r0 + idx / pk;
         const int a = (int)(idx % pk);
         double dx = 0.0, dr = 0.0;
+#pragma unroll 8
         for (int b = 0; b < pk; ++b) {
           const double t = Ts[b * kLd + a];
           dx = fma(ldcg(D + i * p + b), t, dx);
@@ -1336,6 +1435,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         const int64_t i = r0 + idx / pk;
         const int a = (int)(idx % pk);
         double acc = 0.0;
+#pragma unroll 8
         for (int b = 0; b < pk; ++b) acc = fma(ldcg(D + i * p + b), Ts[b * kLd + a], acc);
         Dn[i * p + a] = ldcg(prm.R + i * p + a) + acc;
       }

@@ -14,8 +14,8 @@ namespace ccg {
 namespace tc {
 
 // Kinds of quantised A: BF16; FP8 E4M3 with row scales (operand as two E4M3
-// terms); FP32 multiplied as three TF32 products (A_hi D_hi + A_hi D_lo +
-// A_lo D_hi, the low parts split off in shared memory / at conversion).
+// terms); FP32 multiplied from TF32 halves, (A_hi + A_lo)(D_hi + D_lo) (the
+// low parts split off in shared memory / at conversion).
 enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1, KIND_TF32X3 = 2 };
 
 constexpr int kBM = 128;          // rows per tile (MMA M)
@@ -30,7 +30,10 @@ struct Shape {
   static constexpr int kTileBBytes = NB * kRowBytes;
   static constexpr int kTileA2Bytes = (KIND == KIND_TF32X3) ? kTileABytes : 0;  // A_lo
   static constexpr int kStageBytes = kTileABytes + kTileBBytes;  // bytes one TMA stage brings
-  static constexpr int kTmemCols = (2 * NP < 32) ? 32 : 2 * NP;  // two accumulators
+  // one MMA covers the operand's hi and lo rows at once (N = NB); the epilogue
+  // adds the two halves of the accumulator
+  static constexpr int NMMA = NB;
+  static constexpr int kTmemCols = (2 * NMMA < 32) ? 32 : 2 * NMMA;  // two accumulators
   static constexpr int kRingBytes = kStagesK * (kTileABytes + kTileA2Bytes + kTileBBytes);
   static constexpr int kElemBytes = (KIND == KIND_BF16) ? 2 : (KIND == KIND_FP8) ? 1 : 4;
 };
@@ -158,6 +161,10 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+  } else if constexpr (N == 64) {
+    tmem_ld<32>(taddr, *reinterpret_cast<float(*)[32]>(&v[0]));
+    tmem_ld<32>(taddr + 32u, *reinterpret_cast<float(*)[32]>(&v[32]));
+    return;
   } else {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"

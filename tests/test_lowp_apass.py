@@ -66,7 +66,7 @@ def tf32_trunc(x32):
 
 def reference(torch, A, V, fmt):
     if fmt == 2:
-        # FP32 A; three TF32 products A_hi D_hi + A_hi D_lo + A_lo D_hi with
+        # FP32 A; the four TF32 products (A_hi + A_lo)(D_hi + D_lo) with
         # hi = tf32(x), lo = tf32(x - hi) (x rounded to FP32 first)
         Af = A.astype(np.float32)
         Ah = tf32_trunc(Af)
@@ -74,8 +74,8 @@ def reference(torch, A, V, fmt):
         Vf = V.astype(np.float32)
         Vh = tf32_trunc(Vf)
         Vl = tf32_trunc((Vf.astype(np.float64) - Vh).astype(np.float32))
-        W = Ah @ Vh + Ah @ Vl + Al @ Vh
-        mag = np.abs(Ah) @ np.abs(Vh) + np.abs(Ah) @ np.abs(Vl) + np.abs(Al) @ np.abs(Vh)
+        W = Ah @ Vh + Ah @ Vl + Al @ Vh + Al @ Vl
+        mag = (np.abs(Ah) + np.abs(Al)) @ (np.abs(Vh) + np.abs(Vl))
         return W, mag
     if fmt == 0:
         Aq = bf16_round(torch, A)
@@ -109,9 +109,9 @@ def test_lowp_block_product(env, fmt, n, q):
     ref, mag = reference(torch, A, V, fmt)
     err = np.abs(W.cpu().numpy() - ref)
     if fmt == 2:
-        # 3 MMAs per 8 k (K = 8 per TF32 MMA); plus the TF32 reading of the low
+        # 2 MMAs per 8 k (K = 8 per TF32 MMA); plus the TF32 reading of the low
         # parts (truncation or rounding: one TF32 ulp of a low part)
-        bound = 2.0 * (3 * n / 8 + 8) * 2.0 ** -24 * mag + 2.0 ** -19 * mag
+        bound = 2.0 * (2 * n / 8 + 8) * 2.0 ** -24 * mag + 2.0 ** -19 * mag
         # and the product is FP32-accurate against the exact FP64 one
         exact = np.abs(W.cpu().numpy() - A @ V)
         assert np.all(exact <= 2.0 ** -16 * (np.abs(A) @ np.abs(V)))
