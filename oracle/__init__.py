@@ -79,7 +79,7 @@ def _load():
             lib.oracle_ccg.argtypes = [
                 ctypes.c_int64, _DP, ctypes.c_int64, _DP, _DP, ctypes.c_int,
                 ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                ctypes.c_int, _DP, _DP, _IP, ctypes.POINTER(OracleStats),
+                ctypes.c_int, ctypes.c_int, _DP, _DP, _IP, ctypes.POINTER(OracleStats),
                 TRACE_FN, ctypes.c_void_p]
             lib.oracle_splitmix64_at.restype = ctypes.c_uint64
             lib.oracle_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
@@ -128,7 +128,8 @@ def true_relres(A, b, x, nthreads: int = 1) -> float:
 
 
 def ccg(A, b, X0, tol: float, maxit: int, rank_tol: float = 1e-12,
-        residual_replacement: bool = True, nthreads: int = 1, trace: bool = False):
+        residual_replacement: bool = True, nthreads: int = 1, trace: bool = False,
+        explicit_residual: bool = False):
     """Run the oracle cCG/mcCG on A x = b from the initial block X0 (n x p).
 
     Returns a dict with x, X (final active block), agents (original indices of
@@ -166,7 +167,8 @@ def ccg(A, b, X0, tol: float, maxit: int, rank_tol: float = 1e-12,
 
     cb = TRACE_FN(_cb) if trace else TRACE_FN()
     rc = _load().oracle_ccg(n, _dp(A), lda, _dp(b), _dp(X0), p, float(tol), int(maxit),
-                            float(rank_tol), int(bool(residual_replacement)), int(nthreads),
+                            float(rank_tol), int(bool(residual_replacement)),
+                            int(bool(explicit_residual)), int(nthreads),
                             _dp(x), _dp(Xf), agents.ctypes.data_as(_IP), ctypes.byref(st),
                             cb, None)
     pf = st.p_final

@@ -30,6 +30,9 @@
  *   - "1_p^T b" is read as b 1_p^T (b in every column).
  *   - The residual is carried by the recurrence (Table 1 counts one n^2
  *     product per iteration); the true residual b - A x is computed at exit.
+ *     With explicit_residual set, R_{k+1} = A X_{k+1} - b 1^T is formed
+ *     explicitly each iteration, as Algorithm 2 prints it (a second product
+ *     with A per iteration, as in Algorithm 4).
  *     If it is above tol, the residual is replaced (R = A X - b 1^T, D = R)
  *     and the iteration continues (optional).
  *   - Rank test: Cholesky of the unit-diagonal scaled Gram
@@ -350,7 +353,8 @@ double oracle_true_relres(int64_t n, const double* A, int64_t lda,
 /* ------------------------------------------------------------------------ */
 int oracle_ccg(int64_t n, const double* A, int64_t lda, const double* b,
                const double* X0, int p, double tol, int maxit,
-               double rank_tol, int residual_replacement, int nthreads,
+               double rank_tol, int residual_replacement, int explicit_residual,
+               int nthreads,
                double* x_out, double* X_out, int* agents_out,
                oracle_stats* st, oracle_trace_fn cb, void* cb_ctx)
 {
@@ -472,7 +476,14 @@ int oracle_ccg(int64_t n, const double* A, int64_t lda, const double* b,
         for (int a = 0; a < pk; ++a)
             for (int c = 0; c < pk; ++c) alphaT[c * pk + a] = alpha[a * pk + c];
         add_block_times(n, pk, X, D, alphaT);
-        add_block_times(n, pk, R, W, alphaT);
+        if (explicit_residual) {
+            /* Algorithm 2 as printed: R_{k+1} = A X_{k+1} - b 1^T */
+            mat_block(n, A, lda, X, pk, R, nthreads);
+            for (int64_t i = 0; i < n; ++i)
+                for (int j = 0; j < pk; ++j) R[i * pk + j] -= b[i];
+        } else {
+            add_block_times(n, pk, R, W, alphaT);
+        }
 
         /* beta_k = -R_{k+1}^T W M^{-1} ; D_{k+1} = R_{k+1} + D beta^T */
         gram(n, pk, R, W, H);

@@ -415,3 +415,82 @@ def test_true_relres_helper_matches_numpy(oracle_mod):
     x = wl.random_block(37, 1, seed=18)[:, 0]
     ref = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
     assert abs(oracle_mod.true_relres(A, b, x) - ref) <= 1e-14 * ref
+
+
+# --------------------------------------------------------------------------
+# Explicit residual: Algorithm 2 as printed forms R_{k+1} = A X_{k+1} - b 1^T
+# (a second product with A per iteration, as Algorithm 4 does); the proof of
+# Theorem 2 shows it equals the recurrence in exact arithmetic.
+# --------------------------------------------------------------------------
+
+def textbook_cg_recomputed(A, b, x0, iters):
+    """Textbook CG whose residual is recomputed as b - A x at every step."""
+    x = x0.astype(np.float64).copy()
+    r = b - A @ x
+    d = r.copy()
+    out = [x.copy()]
+    rr = r @ r
+    for _ in range(iters):
+        if rr == 0.0:
+            break
+        Ad = A @ d
+        a = rr / (d @ Ad)
+        x = x + a * d
+        r = b - A @ x
+        rr_new = r @ r
+        d = r + (rr_new / rr) * d
+        rr = rr_new
+        out.append(x.copy())
+    return out
+
+
+def test_explicit_residual_p1_equals_textbook_cg(oracle_mod):
+    n = 64
+    A, b = wl.random_spd(n, seed=21, cond=30.0)
+    x0 = wl.random_block(n, 1, seed=22)[:, 0]
+    r = oracle_mod.ccg(A, b, x0[:, None], tol=1e-10, maxit=500, trace=True,
+                       residual_replacement=False, explicit_residual=True)
+    xs_cg = textbook_cg_recomputed(A, b, x0, 14)
+    for st in r["trace"][1:15]:
+        k = st["k"]
+        assert np.linalg.norm(st["X"][:, 0] - xs_cg[k]) <= 1e-12 * np.linalg.norm(xs_cg[k]), k
+    it = 0
+    for it, xc in enumerate(textbook_cg_recomputed(A, b, x0, 500)):
+        if np.linalg.norm(A @ xc - b) <= 1e-10 * np.linalg.norm(b):
+            break
+    assert abs(r["iterations"] - it) <= 1
+
+
+@pytest.mark.parametrize("n,p,cond", [(30, 3, 1e3), (64, 4, 1e3), (33, 8, 1e2)])
+def test_explicit_residual_direct_solve(oracle_mod, n, p, cond):
+    A, b = wl.random_spd(n, seed=n + 7 * p, cond=cond)
+    X0 = wl.random_block(n, p, seed=2)
+    r = oracle_mod.ccg(A, b, X0, tol=1e-13, maxit=10 * n, explicit_residual=True)
+    assert r["status"] == 0, r["status_name"]
+    xs = np.linalg.solve(A, b)
+    assert np.linalg.norm(r["x"] - xs) / np.linalg.norm(xs) <= 1e-10
+
+
+def test_explicit_residual_trace_is_the_true_residual(oracle_mod):
+    n, p = 40, 3
+    A, b = wl.random_spd(n, seed=31, cond=100.0)
+    X0 = wl.random_block(n, p, seed=32)
+    r = oracle_mod.ccg(A, b, X0, tol=1e-12, maxit=200, trace=True,
+                       residual_replacement=False, explicit_residual=True)
+    for st in r["trace"]:
+        true = A @ st["X"] - b[:, None]
+        scale = np.abs(A) @ np.abs(st["X"]) + np.abs(b)[:, None]
+        assert np.all(np.abs(st["R"] - true) <= 1e-13 * scale), st["k"]
+
+
+def test_explicit_and_recurrence_forms_agree_early(oracle_mod):
+    n, p = 60, 4
+    A, b = wl.random_spd(n, seed=41, cond=100.0)
+    X0 = wl.random_block(n, p, seed=42)
+    kw = dict(tol=1e-12, maxit=200, trace=True, residual_replacement=False)
+    r1 = oracle_mod.ccg(A, b, X0, **kw)
+    r2 = oracle_mod.ccg(A, b, X0, explicit_residual=True, **kw)
+    for s1, s2 in zip(r1["trace"][1:6], r2["trace"][1:6]):
+        assert np.array_equal(s1["agents"], s2["agents"])
+        assert np.linalg.norm(s1["X"] - s2["X"]) <= 1e-11 * np.linalg.norm(s1["X"])
+    assert abs(r1["iterations"] - r2["iterations"]) <= 2
