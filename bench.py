@@ -163,6 +163,13 @@ class ClockSampler:
                 "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def p_bucket(p):
+    q = 1
+    while q < p:
+        q *= 2
+    return q
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -201,13 +208,12 @@ def device_exp_kernel(n, seed, length, nugget, dev):
     return A
 
 
-def lowp_roofline(ccg, solver, dev, n, p, hbm_gbs, steps=10):
-    """HBM bandwidth of the tensor-core block product (BF16 and FP8 A) at
-    n = 32768 (the precision workload: exponential kernel, length 0.1,
-    nugget 1e-3, seed 2)."""
+def lowp_roofline(ccg, solver, dev, A, p, hbm_gbs, steps=10):
+    """HBM bandwidth of the tensor-core block product (BF16 and FP8 A) on the
+    precision workload (exponential kernel, length 0.1, nugget 1e-3, seed 2)."""
     import numpy as np
     import torch
-    A = device_exp_kernel(n, 2, 0.1, 1e-3, dev)
+    n = A.shape[0]
     out = {}
     for fmt, name in [(ccg.LOWP_BF16, "bf16"), (ccg.LOWP_FP8_E4M3, "fp8_e4m3")]:
         m = solver.lowp_matrix(A, fmt)
@@ -221,8 +227,6 @@ def lowp_roofline(ccg, solver, dev, n, p, hbm_gbs, steps=10):
         out[name] = {"n": n, "p": p, "ms": ms, "bytes": m.nbytes(), "gbs": gbs,
                      "frac_of_measured_hbm": gbs / hbm_gbs if hbm_gbs else None}
         m.close()
-    del A
-    torch.cuda.empty_cache()
     return out
 
 
@@ -259,10 +263,78 @@ def mixed_lines(ccg, dev, stream, A, b, p, steps, tol=TOL):
     return out
 
 
+def p_sweep(ccg, solver, stream, dA, db, x, n, ps=(1, 4, 8, 16, 32)):
+    """FP64 cCG on the benchmark system for every agent count of the sweep:
+    one warm-up and one timed solve each."""
+    import torch
+    out = {}
+    for p in ps:
+        solver.solve(dA, db, x, p=p, tol=TOL, maxit=20 * n)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = solver.solve(dA, db, x, p=p, tol=TOL, maxit=20 * n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[str(p)] = {"solves_per_s": 1e3 / ms, "ms": ms, "iterations": r.iterations,
+                       "status": r.status_name, "relres_true": r.relres_true,
+                       "ms_per_iteration": r.device_ms / max(r.iterations, 1)}
+    return out
+
+
+def precision_lines(ccg, stream, A, p=16, tol=TOL, seed=2):
+    """The precision workload at full size: A (FP64, on the device) is the
+    exponential kernel on n points (length 0.1, nugget 1e-3), b ~ N(0, 1);
+    FP64 cCG, then FP32 / BF16 / FP8 A inside FP64 refinement.  Each line
+    states its true relative residual and its distance to the FP64 solution."""
+    import numpy as np
+    import torch
+    n = A.shape[0]
+    dev = A.device
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    b = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    bn = float(torch.linalg.vector_norm(b))
+    out = {"workload": f"exponential kernel, n = {n} points U[0,1]^3 (seed {seed}), length 0.1, "
+                       f"nugget 1e-3, b ~ N(0,1), p = {p}, tol {tol}", "n": n, "p": p}
+    x64 = None
+    for name, prec, reps in [("fp64", ccg.FP64, 1), ("fp32_ir", ccg.FP32_IR, 2),
+                             ("bf16_ir", ccg.BF16_IR, 1), ("fp8_ir", ccg.FP8_IR, 1)]:
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        with ccg.Solver(stream=stream.cuda_stream, precision=prec,
+                        max_outer=0 if prec in (ccg.FP64, ccg.FP32_IR) else 12) as s:
+            s.solve(A, b, x, p=p, tol=tol, maxit=2)  # warm-up (kernels, workspace)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rs = [s.solve(A, b, x, p=p, tol=tol, maxit=20000) for _ in range(reps)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        r = rs[-1]
+        relres = float(torch.linalg.vector_norm(b - A @ x)) / bn
+        line = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "status": r.status_name,
+                "iterations": r.iterations, "outer_steps": r.outer_steps,
+                "relres_true": relres}
+        if x64 is None:
+            x64 = x.clone()
+        else:
+            line["err_vs_fp64"] = float(torch.linalg.vector_norm(x - x64) /
+                                        torch.linalg.vector_norm(x64))
+        out[name] = line
+    for k in ("fp32_ir", "bf16_ir", "fp8_ir"):
+        out[f"speedup_{k}_vs_fp64"] = (out[k]["solves_per_s"] / out["fp64"]["solves_per_s"]
+                                       if out[k]["status"] == "CCG_OK" else None)
+    return out
+
+
 def batched_line(ccg, dev, stream, count=4096, p=4, seed=3):
     """4096 independent systems, n log-uniform in [32, 1024], A = G G^T / n +
-    s I with s ~ U(0.05, 1), b ~ N(0, 1) (generated on the device), FP64,
-    one persistent launch."""
+    s I with s ~ U(0.05, 1), b ~ N(0, 1) (generated on the device), one
+    persistent launch each in FP64 and in FP32 + FP64 refinement."""
     import numpy as np
     import torch
     rng = np.random.default_rng(seed)
@@ -279,19 +351,28 @@ def batched_line(ccg, dev, stream, count=4096, p=4, seed=3):
         blk[:, :n] = G @ G.T / n
         blk.diagonal().add_(float(sh))
     bp = torch.randn(vt, dtype=torch.float64, device=dev, generator=g)
-    x = torch.zeros_like(bp)
-    with ccg.Solver(stream=stream.cuda_stream) as s:
-        s.solve_batched(sizes, Ap, bp, x, p=p, tol=TOL, maxit=20000)   # warm-up
-        summ, st, it, rr = s.solve_batched(sizes, Ap, bp, x, p=p, tol=TOL, maxit=20000)
     nsq = float(np.sum(np.array(sizes, dtype=np.float64) ** 2))
-    t = summ.device_ms / 1e3
-    flops = float(np.sum(2.0 * np.array(sizes, dtype=np.float64) ** 2 * p * it))
-    return {"workload": f"{count} systems, n log-uniform [32, 1024], A = G G^T/n + U(0.05,1) I, "
-                        f"p = {p}, FP64, one launch", "systems": count,
-            "solves_per_s": count / t, "ms": summ.device_ms, "status": summ.status_name,
-            "all_ok": bool(np.all(st == 0)), "max_relres": float(np.max(rr)),
-            "iterations_total": int(np.sum(it)), "fp64_tflops": flops / t / 1e12,
-            "a_bytes": 8.0 * nsq, "ctas": summ.ctas}
+    out = {"workload": f"{count} systems, n log-uniform [32, 1024], A = G G^T/n + U(0.05,1) I, "
+                       f"p = {p}, tol 1e-10, one launch per batch", "systems": count,
+           "a_bytes_fp64": 8.0 * nsq}
+    for name, prec in (("fp64", ccg.FP64), ("fp32_ir", ccg.FP32_IR)):
+        x = torch.zeros_like(bp)
+        with ccg.Solver(stream=stream.cuda_stream, precision=prec) as s:
+            s.solve_batched(sizes, Ap, bp, x, p=p, tol=TOL, maxit=20000)   # warm-up
+            summ, st, it, rr = s.solve_batched(sizes, Ap, bp, x, p=p, tol=TOL, maxit=20000)
+        t = summ.device_ms / 1e3
+        line = {"solves_per_s": count / t, "ms": summ.device_ms, "status": summ.status_name,
+                "all_ok": bool(np.all(st == 0)), "max_relres": float(np.max(rr)),
+                "iterations_total": int(np.sum(it)), "ctas": summ.ctas}
+        if prec == ccg.FP64:
+            flops = float(np.sum(2.0 * np.array(sizes, dtype=np.float64) ** 2 * p * it))
+            line["fp64_tflops"] = flops / t / 1e12
+        else:
+            line["outer_steps_max"] = summ.outer_steps
+        out[name] = line
+    out["speedup_fp32_ir_vs_fp64"] = (out["fp32_ir"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+                                      if out["fp32_ir"]["all_ok"] else None)
+    return out
 
 
 def serving_line(ccg, dev, precision, count=48, rate=2000.0, seed=4, workers=8):
@@ -510,11 +591,16 @@ def main():
                "h2d_bytes_per_step": int(A.nbytes + b.nbytes),
                "d2h_bytes_per_step": int(8 * n + 192)}
 
-    mixed = lowp = batched = serving = None
+    mixed = lowp = batched = serving = sweep = precision = None
     if rank == 0 and not args.no_mixed:
         from paper_1204_0069_gb300 import workloads as wl
         peaks0 = measured_peaks()
-        lowp = lowp_roofline(ccg, solver, dev, args.lowp_n, 16, peaks0.get("hbm_gbs"))
+        sweep = p_sweep(ccg, solver, stream, dA, db, x, n)
+        A3 = device_exp_kernel(args.lowp_n, 2, 0.1, 1e-3, dev)
+        lowp = lowp_roofline(ccg, solver, dev, A3, 16, peaks0.get("hbm_gbs"))
+        precision = precision_lines(ccg, stream, A3, p=16)
+        del A3
+        torch.cuda.empty_cache()
         mixed = {"exp_kernel_n8192": mixed_lines(ccg, dev, stream, A, b, p, 2)}
         Ag, bg = wl.gram_shift(n, seed=3, shift=0.5)
         mixed["gram_shift_n8192"] = mixed_lines(ccg, dev, stream, Ag, bg, p, 3)
@@ -554,7 +640,7 @@ def main():
                            "p99": float(np.percentile(kernel_ms, 99))},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
-                         "kernel": "fp64_kernel<8,true> (persistent solve)",
+                         "kernel": f"fp64_kernel<{p_bucket(p)},true> (persistent solve)",
                          "peak_note": "nominal FP64 rate (FP64 pipe bound)"},
             "apass": {"ms": bp_ms, "gbs": 8.0 * n * n / (bp_ms / 1e3) / 1e9,
                       "tflops": 2.0 * n * n * p / (bp_ms / 1e3) / 1e12,
@@ -563,8 +649,12 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk,
         }
+        if sweep is not None:
+            line["p_sweep"] = sweep
         if lowp is not None:
             line["lowp_apass"] = lowp
+        if precision is not None:
+            line["precision"] = precision
         if mixed is not None:
             line["mixed"] = mixed
         if batched is not None:

@@ -79,6 +79,12 @@ typedef struct {
                                    inner solve; 0 = 1e-4 (FP32), 1e-2 (BF16),
                                    1e-1 (FP8)                                 */
     int max_outer;              /* mixed precision: refinement steps; 0 = 60 */
+    int explicit_residual;      /* 1: form R_{k+1} = A X_{k+1} - b 1' by a second
+                                   product with A each iteration, as Algorithm 2
+                                   prints it, instead of the recurrence
+                                   R_{k+1} = R_k + A D_k alpha_k' (default 0).
+                                   Doubles the A traffic.  CCG_FP64 only:
+                                   CCG_ERR_INVALID with a mixed precision.   */
 } ccg_config;
 
 typedef struct {
@@ -244,9 +250,22 @@ int ccg_lowp_destroy(ccg_lowp_matrix* m);
  *               first non-OK status; iterations = sum over systems;
  *               device_ms = time of the launch; ctas = grid size.
  * Each system uses the handle's configuration (x0 = 0 with the initial-block
- * spread, residual replacement, rank tolerance).  Errors: CCG_ERR_INVALID
- * (count < 0, bad sizes, host pointers for A, b, x_out), CCG_ERR_OOM,
- * CCG_ERR_CUDA.
+ * spread, residual replacement, rank tolerance).
+ *
+ * Precision (handle configuration): CCG_FP64 solves each system in FP64.
+ * CCG_FP32_IR solves each system by FP64 iterative refinement (r = b - A x
+ * and the update of x in FP64) around inner cCG solves on an FP32 copy of
+ * A_i whose block product runs on the FP32 pipe; the copy is made inside
+ * the launch.  The inner tolerance is cfg.inner_tol (0 = 1e-5), at most
+ * cfg.max_outer refinement steps (0 = 30); refinement stops early when two
+ * steps in a row do not reduce the true residual, and each x_i is the best
+ * iterate.  relres[i] is the true relative residual of that x_i;
+ * iterations[i] counts inner cCG iterations; summary->outer_steps is the
+ * largest number of refinement steps of any system.  CCG_BF16_IR and
+ * CCG_FP8_IR are not offered here (CCG_ERR_INVALID).
+ *
+ * Errors: CCG_ERR_INVALID (count < 0, bad sizes, host pointers for A, b,
+ * x_out, unsupported precision), CCG_ERR_OOM, CCG_ERR_CUDA.
  */
 int ccg_solve_batched(ccg_handle* handle, int64_t count, const int64_t* n, const double* A,
                       const double* b, int p, double tol, int maxit, double* x_out,

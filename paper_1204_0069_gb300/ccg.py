@@ -36,7 +36,8 @@ class Config(ctypes.Structure):
                 ("x0_spread", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("residual_replacement", ctypes.c_int),
                 ("barrier_timeout_ms", ctypes.c_double), ("max_ctas", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("explicit_residual", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -182,7 +183,7 @@ class Solver:
     def __init__(self, device: int = 0, stream=None, rank_tol: float = 1e-12,
                  x0_spread: float = 1.0, seed: int = 0, residual_replacement: bool = True,
                  barrier_timeout_ms: float = 10000.0, max_ctas: int = 0, precision: int = 0,
-                 inner_tol: float = 0.0, max_outer: int = 0):
+                 inner_tol: float = 0.0, max_outer: int = 0, explicit_residual: bool = False):
         L = lib()
         cfg = Config()
         L.ccg_config_init(ctypes.byref(cfg))
@@ -197,6 +198,7 @@ class Solver:
         cfg.precision = precision
         cfg.inner_tol = inner_tol
         cfg.max_outer = max_outer
+        cfg.explicit_residual = int(bool(explicit_residual))
         h = _VP()
         rc = L.ccg_create(ctypes.byref(h), ctypes.byref(cfg))
         if rc != 0:

@@ -1,6 +1,7 @@
 // ccg_batch.cu -- C ABI of the batched solver (include/ccg.h:
 // ccg_solve_batched): argument checks, the largest-first queue of system
-// descriptors, workspace, one launch, and the per-system results.
+// descriptors, workspace (plus the FP32 copies and refinement vectors of the
+// mixed-precision variant), one launch, and the per-system results.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,19 +61,27 @@ extern "C" int ccg_solve_batched(ccg_handle* h, int64_t count, const int64_t* n,
     desc[4 * k + 3] = i;
   }
 
+  const bool ir = h->cfg.precision == CCG_FP32_IR;
+  if (!ir && h->cfg.precision != CCG_FP64) return fail(CCG_ERR_INVALID);
   const int P = ccg::p_bucket(p);
-  const int per_sm = ccg::batch_ctas_per_sm(P);
+  const int per_sm = ccg::batch_ctas_per_sm(P, ir);
   if (per_sm < 1) return fail(CCG_ERR_CUDA);
   int G = h->num_sms * per_sm;
   if (h->cfg.max_ctas > 0) G = std::min(G, h->cfg.max_ctas);
   G = (int)std::max<int64_t>(1, std::min<int64_t>(G, count));
   const int64_t slot = 5 * nmax * p;
+  // refinement slots: r, b_in, delta, x_best; FP32 A copy and operand rows
+  const int64_t ld32 = (nmax + 3) & ~int64_t(3);
+  const int64_t vslot = ir ? 4 * nmax : 0;
+  const int64_t fslot = ir ? (nmax + P) * ld32 : 0;
   int rc = ensure(&h->ws, &h->ws_bytes,
                   Carve::need({(size_t)G * slot * sizeof(double),
                                (size_t)G * ccg::kPartStride * sizeof(double),
                                (size_t)G * sizeof(ccg::DevState), desc.size() * sizeof(int64_t),
                                sizeof(unsigned), (size_t)count * sizeof(int),
-                               (size_t)count * sizeof(int), (size_t)count * sizeof(double)}));
+                               (size_t)count * sizeof(int), (size_t)count * sizeof(double),
+                               (size_t)count * sizeof(int), (size_t)G * vslot * sizeof(double),
+                               (size_t)G * fslot * sizeof(float)}));
   if (rc != CCG_OK) return fail(rc);
   Carve wc(h->ws);
   double* X = wc.take<double>((size_t)G * slot);
@@ -83,6 +92,9 @@ extern "C" int ccg_solve_batched(ccg_handle* h, int64_t count, const int64_t* n,
   int* dstatus = wc.take<int>(count);
   int* diters = wc.take<int>(count);
   double* drelres = wc.take<double>(count);
+  int* douter = wc.take<int>(count);
+  double* vbuf = wc.take<double>((size_t)G * vslot);
+  float* fbuf = wc.take<float>((size_t)G * fslot);
 
   cudaStream_t s = h->stream;
   cudaError_t e = cudaMemcpyAsync(ddesc, desc.data(), desc.size() * sizeof(int64_t),
@@ -117,11 +129,20 @@ extern "C" int ccg_solve_batched(ccg_handle* h, int64_t count, const int64_t* n,
   prm.batch_status = dstatus;
   prm.batch_iters = diters;
   prm.batch_relres = drelres;
+  if (ir) {
+    prm.batch_vec = vbuf;
+    prm.batch_vec_stride = vslot;
+    prm.batch_f32 = fbuf;
+    prm.batch_f32_stride = fslot;
+    prm.batch_inner_tol = h->cfg.inner_tol > 0.0 ? h->cfg.inner_tol : 1e-5;
+    prm.batch_max_outer = h->cfg.max_outer > 0 ? h->cfg.max_outer : 30;
+    prm.batch_outer = douter;
+  }
 
   e = cudaEventRecord(h->ev0, s);
-  if (e == cudaSuccess) e = ccg::launch_batch(prm, P, G, s);
+  if (e == cudaSuccess) e = ccg::launch_batch(prm, P, G, s, ir);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev1, s);
-  std::vector<int> hs(count), hi(count);
+  std::vector<int> hs(count), hi(count), ho(count, 0);
   std::vector<double> hr(count);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(hs.data(), dstatus, count * sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -129,16 +150,20 @@ extern "C" int ccg_solve_batched(ccg_handle* h, int64_t count, const int64_t* n,
     e = cudaMemcpyAsync(hi.data(), diters, count * sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(hr.data(), drelres, count * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && ir)
+    e = cudaMemcpyAsync(ho.data(), douter, count * sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(map_cuda(e));
   int worst = CCG_OK;
   long long total = 0;
+  int max_outer = 0;
   for (int64_t i = 0; i < count; ++i) {
     if (status) status[i] = hs[i];
     if (iterations) iterations[i] = hi[i];
     if (relres) relres[i] = hr[i];
     if (worst == CCG_OK && hs[i] != CCG_OK) worst = hs[i];
     total += hi[i];
+    max_outer = std::max(max_outer, ho[i]);
   }
   if (summary) {
     summary->status = worst;
@@ -147,6 +172,7 @@ extern "C" int ccg_solve_batched(ccg_handle* h, int64_t count, const int64_t* n,
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     summary->device_ms = ms;
     summary->ctas = G;
+    summary->outer_steps = max_outer;
   }
   return worst;
 }

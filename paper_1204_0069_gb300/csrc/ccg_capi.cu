@@ -147,6 +147,7 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
   prm.tol = tol;
   prm.rank_tol = h->cfg.rank_tol;
   prm.replacement = h->cfg.residual_replacement ? 1 : 0;
+  prm.explicit_residual = h->cfg.explicit_residual ? 1 : 0;
   prm.mode = ccg::MODE_SOLVE;
   prm.timeout_ns = (long long)(h->cfg.barrier_timeout_ms * 1e6);
   prm.expected_ctas = (unsigned)G;
@@ -206,6 +207,7 @@ void ccg_config_init(ccg_config* cfg) {
   cfg->max_ctas = 0;
   cfg->inner_tol = 0.0;
   cfg->max_outer = 0;
+  cfg->explicit_residual = 0;
 }
 
 int ccg_create(ccg_handle** out, const ccg_config* cfg) {
@@ -217,7 +219,9 @@ int ccg_create(ccg_handle** out, const ccg_config* cfg) {
   if (!(c.rank_tol > 0.0) || !(c.barrier_timeout_ms > 0.0) ||
       (c.precision != CCG_FP64 && c.precision != CCG_FP32_IR && c.precision != CCG_BF16_IR &&
        c.precision != CCG_FP8_IR) ||
-      c.max_ctas < 0 || c.inner_tol < 0.0 || c.max_outer < 0)
+      c.max_ctas < 0 || c.inner_tol < 0.0 || c.max_outer < 0 ||
+      (c.explicit_residual != 0 && c.explicit_residual != 1) ||
+      (c.explicit_residual && c.precision != CCG_FP64))
     return CCG_ERR_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {

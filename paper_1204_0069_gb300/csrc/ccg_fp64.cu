@@ -29,22 +29,28 @@ void* select_any(int P, bool vec, int pol) {
   return pol == POL_FP64 ? select_kernel(P, vec) : select_kernel_lp(P, pol);
 }
 
-void* select_batch(int P) {
+void* select_batch(int P, bool ir) {
   switch (P) {
-    case 1: return reinterpret_cast<void*>(&batch_kernel<1>);
-    case 2: return reinterpret_cast<void*>(&batch_kernel<2>);
-    case 4: return reinterpret_cast<void*>(&batch_kernel<4>);
-    case 8: return reinterpret_cast<void*>(&batch_kernel<8>);
-    case 16: return reinterpret_cast<void*>(&batch_kernel<16>);
-    case 32: return reinterpret_cast<void*>(&batch_kernel<32>);
+    case 1: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<1>)
+                      : reinterpret_cast<void*>(&batch_kernel<1>);
+    case 2: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<2>)
+                      : reinterpret_cast<void*>(&batch_kernel<2>);
+    case 4: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<4>)
+                      : reinterpret_cast<void*>(&batch_kernel<4>);
+    case 8: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<8>)
+                      : reinterpret_cast<void*>(&batch_kernel<8>);
+    case 16: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<16>)
+                       : reinterpret_cast<void*>(&batch_kernel<16>);
+    case 32: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<32>)
+                       : reinterpret_cast<void*>(&batch_kernel<32>);
     default: return nullptr;
   }
 }
 
 }  // namespace
 
-int batch_ctas_per_sm(int P) {
-  void* fn = select_batch(P);
+int batch_ctas_per_sm(int P, bool ir) {
+  void* fn = select_batch(P, ir);
   if (!fn) return 0;
   const size_t smem = fp64_smem_bytes(P, POL_FP64);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -54,8 +60,8 @@ int batch_ctas_per_sm(int P) {
   return nb;
 }
 
-cudaError_t launch_batch(const Params& prm, int P, int ctas, cudaStream_t stream) {
-  void* fn = select_batch(P);
+cudaError_t launch_batch(const Params& prm, int P, int ctas, cudaStream_t stream, bool ir) {
+  void* fn = select_batch(P, ir);
   if (!fn) return cudaErrorInvalidValue;
   const size_t smem = fp64_smem_bytes(P, POL_FP64);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -38,9 +38,11 @@ enum Mode : int {
   MODE_REFINE = 3      // x += c delta; r = b - A x (FP64); scaled residual
 };
 
-// A-pass policy of the persistent kernel: FP64 A on the FP64 pipe, or a
-// quantised A on the tensor cores (inner solves of the mixed-precision path).
-enum Policy : int { POL_FP64 = 0, POL_BF16 = 1, POL_FP8 = 2, POL_TF32X3 = 3 };
+// A-pass policy of the persistent kernel: FP64 A on the FP64 pipe, a
+// quantised A on the tensor cores (inner solves of the mixed-precision path),
+// or an FP32 copy of A on the FP32 pipe (inner solves of the batched
+// mixed-precision path).
+enum Policy : int { POL_FP64 = 0, POL_BF16 = 1, POL_FP8 = 2, POL_TF32X3 = 3, POL_F32 = 4 };
 
 // Status values mirror ccg_status in include/ccg.h.
 enum Status : int {
@@ -86,6 +88,7 @@ struct DevState {
   double gram_out[2 * kSq]; // block-product mode: M, G (stride kMaxP)
   float sigma[kMaxP];       // FP8 operand column scales
   double rnorm;             // refinement mode: ||b - A x||
+  double red[kPartHalf];    // cross-CTA sums of the partial slots (same offsets)
 };
 
 struct Params {
@@ -111,6 +114,7 @@ struct Params {
   double tol;
   double rank_tol;
   int replacement;
+  int explicit_residual;   // R_{k+1} = A X_{k+1} - b 1^T instead of the recurrence
   int mode;
   long long timeout_ns;
   unsigned int expected_ctas;  // barrier arrival count
@@ -133,6 +137,20 @@ struct Params {
   int* batch_status;
   int* batch_iters;
   double* batch_relres;
+  // batched FP32 refinement: per CTA slot, r, b_in, delta, x_best (n each)
+  // and the FP32 copy of A with the FP32 operand rows
+  double* batch_vec;
+  int64_t batch_vec_stride;    // doubles per slot
+  float* batch_f32;
+  int64_t batch_f32_stride;    // floats per slot
+  double batch_inner_tol;
+  int batch_max_outer;
+  int* batch_outer;            // refinement steps per system
+  // FP32 A-pass (POL_F32): A32 row-major with leading dimension a32_ld (a
+  // multiple of 4), operand columns as FP32 rows vt32 (stride a32_ld)
+  const float* a32;
+  int64_t a32_ld;
+  float* vt32;
   // tensor-core A-pass (policy != POL_FP64)
   int lp_kc;               // k-chunks per 128-row tile
   int lp_kelems;           // K elements per chunk
@@ -161,7 +179,8 @@ int fp64_ctas_per_sm(int P, bool vec, int pol = POL_FP64);
 cudaError_t launch_fp64(const Params& prm, int P, bool vec, int ctas,
                         cudaStream_t stream, int pol = POL_FP64);
 // Batched solver (groups of one CTA): occupancy and launch.
-int batch_ctas_per_sm(int P);
-cudaError_t launch_batch(const Params& prm, int P, int ctas, cudaStream_t stream);
+// ir: the FP32-refinement variant (batch_ir_kernel).
+int batch_ctas_per_sm(int P, bool ir = false);
+cudaError_t launch_batch(const Params& prm, int P, int ctas, cudaStream_t stream, bool ir = false);
 
 }  // namespace ccg

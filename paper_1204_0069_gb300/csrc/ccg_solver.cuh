@@ -9,11 +9,13 @@
 //
 //   A-pass   W = A D_k (own rows; A streamed once per iteration), and the
 //            per-CTA partials of M = D'W, G = R'D           (Table 1, rows 1-3)
-//   sync #1  last-arriving CTA: fixed-order sum of the partials, scaled
-//            Cholesky of M with the rank test of Algorithm 3, alpha_k
+//   sync #1  cross-CTA sums of the partials (spread over all CTAs when there
+//            are many), then in the last-arriving CTA the scaled Cholesky of
+//            M with the rank test of Algorithm 3 and alpha_k
 //   update   X += D alpha^T, R += W alpha^T (recurrence, proof of Thm. 2);
 //            partials of H = R_{k+1}'W and ||R_{k+1} e_j||^2  (Table 1, rows 5-7)
-//   sync #2  last-arriving CTA: beta_k, stop test min_j ||R e_j|| <= tol ||b||
+//   sync #2  cross-CTA sums, then in the last-arriving CTA beta_k and the stop
+//            test min_j ||R e_j|| <= tol ||b||
 //   D-update D_{k+1} = R_{k+1} + D_k beta^T                  (Table 1, row 9)
 //   barrier
 //
@@ -21,9 +23,14 @@
 // exact (Sec. 4 works in exact arithmetic); they decide the matrix stepsizes
 // and the stop test, so they are accumulated with error-free transformations
 // (Dot2 of Ogita, Rump and Oishi 2005: exact products by FMA, TwoSum for the
-// running sum) per CTA and again across CTAs.  All cross-CTA sums run in a
-// fixed order (CTA 0, 1, ...), so a solve is bitwise reproducible for a fixed
-// grid.  Every wait on another CTA gives up
+// running sum) per CTA and again across CTAs.  Every sum runs in an order
+// fixed by the grid alone, so a solve is bitwise reproducible for a fixed
+// grid.  (The inner solves of the mixed-precision path, whose operator is
+// itself a rounded copy of A, accumulate their Grams in plain FP64.)  On
+// GB300 a single SM retires about two FP64 operations per clock, so the
+// serial steps keep their dependent chains short: sums over CTAs are warp
+// trees, and large sets are spread over all CTAs.  Every wait on another CTA
+// gives up
 // after Params::timeout_ns and sets CCG_ERR_TIMEOUT; all CTAs then return.
 #pragma once
 
@@ -432,43 +439,83 @@ __device__ void apass(const Params& prm, const double* __restrict__ V, int ldv,
 // dimension ld:  out[g0 + a*kMaxP + c] = sum_i U0[i,a] V0[i,c]  (U0 != NULL)
 //                out[g1 + a*kMaxP + c] = sum_i U1[i,a] V1[i,c]  (U1 != NULL)
 //                out[kSlotVec + a]    = sum_i S[i,a]^2          (S != NULL)
-// Each entry is one thread's compensated sum over i in row order (hi at
-// [slot], lo at [kPartHalf + slot]).
+// Each entry is summed by a group of T lanes (T = 32 for a few entries, 1
+// when they fill the CTA): lane q of the group takes rows r0 + q, r0 + q + T,
+// ... in order, then the group combines in a fixed butterfly.  COMP: Dot2
+// (hi at [slot], lo at [kPartHalf + slot]); otherwise a plain FP64 sum (lo 0).
+template <bool COMP>
+__device__ __forceinline__ void grp_combine(DSum& t, int T) {
+  for (int m = T >> 1; m >= 1; m >>= 1) {
+    const double oh = __shfl_xor_sync(0xffffffffu, t.hi, m);
+    if constexpr (COMP) {
+      const double ol = __shfl_xor_sync(0xffffffffu, t.lo, m);
+      const bool low = (threadIdx.x & m) == 0;
+      DSum a = low ? t : DSum{oh, ol};
+      const DSum b = low ? DSum{oh, ol} : t;
+      dsum_add(a, b.hi, b.lo);
+      t = a;
+    } else {
+      t.hi = t.hi + oh;
+    }
+  }
+}
+
+template <bool COMP>
 __device__ void partial_grams(const double* U0, const double* V0, const double* U1,
                               const double* V1, const double* S, int ld, int pk,
                               int64_t r0, int64_t r1, double* out) {
   const int sq = pk * pk;
-  const int total = 2 * sq + pk;
-  for (int e = threadIdx.x; e < total; e += kThreads) {
-    const double* U;
-    const double* Vv;
-    int a, c, slot;
-    if (e < sq) {
-      U = U0; Vv = V0; a = e / pk; c = e - a * pk; slot = kSlotGram0 + a * kMaxP + c;
-    } else if (e < 2 * sq) {
-      const int f = e - sq;
-      U = U1; Vv = V1; a = f / pk; c = f - a * pk; slot = kSlotGram1 + a * kMaxP + c;
-    } else {
-      U = S; Vv = S; a = c = e - 2 * sq; slot = kSlotVec + a;
-    }
-    if (U == nullptr) continue;
-    DSum t{0.0, 0.0};
-    int64_t i = r0;
-    // blocks of 8 rows: 16 independent loads in flight, then the compensated
-    // sum in row order (the same order as one row at a time)
-    for (; i + 8 <= r1; i += 8) {
-      double u[8], v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        u[q] = ldcg(U + (i + q) * ld + a);
-        v[q] = ldcg(Vv + (i + q) * ld + c);
+  const int n0 = U0 ? sq : 0, n1 = U1 ? sq : 0, n2 = S ? pk : 0;
+  const int E = n0 + n1 + n2;
+  int T = 1;
+  while (T < 32 && E * T * 2 <= kThreads) T <<= 1;
+  const int groups = kThreads / T;
+  const int gi = threadIdx.x / T, q = threadIdx.x % T;
+  for (int base = 0; base < E; base += groups) {  // same trip count in every warp
+    const int e = base + gi;
+    const bool act = e < E;
+    const double* U = S;
+    const double* Vv = S;
+    int slot = 0, a = 0, c = 0;
+    if (act) {
+      if (e < n0) {
+        U = U0; Vv = V0; a = e / pk; c = e - a * pk; slot = kSlotGram0 + a * kMaxP + c;
+      } else if (e < n0 + n1) {
+        const int f = e - n0;
+        U = U1; Vv = V1; a = f / pk; c = f - a * pk; slot = kSlotGram1 + a * kMaxP + c;
+      } else {
+        a = c = e - n0 - n1; slot = kSlotVec + a;
       }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) dsum_fma(t, u[q], v[q]);
     }
-    for (; i < r1; ++i) dsum_fma(t, ldcg(U + i * ld + a), ldcg(Vv + i * ld + c));
-    out[slot] = t.hi;
-    out[kPartHalf + slot] = t.lo;
+    DSum t{0.0, 0.0};
+    if (act) {
+      int64_t i = r0 + q;
+      // blocks of 8 of this lane's rows: 16 independent loads in flight, then
+      // the sum in row order
+      for (; i + 7 * T < r1; i += 8 * T) {
+        double u[8], v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          u[k] = ldcg(U + (i + k * T) * ld + a);
+          v[k] = ldcg(Vv + (i + k * T) * ld + c);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if constexpr (COMP) dsum_fma(t, u[k], v[k]);
+          else t.hi = fma(u[k], v[k], t.hi);
+        }
+      }
+      for (; i < r1; i += T) {
+        const double uu = ldcg(U + i * ld + a), vv = ldcg(Vv + i * ld + c);
+        if constexpr (COMP) dsum_fma(t, uu, vv);
+        else t.hi = fma(uu, vv, t.hi);
+      }
+    }
+    grp_combine<COMP>(t, T);
+    if (act && q == 0) {
+      out[slot] = t.hi;
+      out[kPartHalf + slot] = COMP ? t.lo : 0.0;
+    }
   }
 }
 
@@ -501,48 +548,126 @@ struct SerialSmem {
   double y[kMaxP * kLd];
   double sc[kMaxP];
   double s2[kMaxP];
+  double sv[kMaxP];
   int keep[kMaxP];
   int flag[4];
+  int chol_m;
+  int chol_fail;
 };
 
-// Compensated sum of a slot entry over the CTAs, in CTA order.
-__device__ __forceinline__ double sum_parts(const Params& prm, int off) {
-  DSum t{0.0, 0.0};
+// Cross-CTA sums.  A serial step needs the group's sum of some slot entries
+// ("reduction set").  Each entry is summed by one warp: lane l takes the
+// partials of CTAs l, l+32, ... in order (compensated), the lanes combine in
+// the fixed butterfly of dsum_warp, and the rounded sum goes to st->red at the
+// entry's slot offset.  The result of an entry does not depend on which warp
+// or CTA sums it.  Small sets are summed by the serial CTA itself; larger
+// ones are spread over the warps of every CTA of the group between two grid
+// barriers, so no single SM carries E x G compensated additions.
+enum RedSet : int {
+  RED_M_G = 0,   // Gram0 and Gram1, q x q each
+  RED_H_S = 1,   // Gram0 (q x q) and the vector slot (q)
+  RED_S = 2,     // vector slot (q)
+  RED_SCALAR = 3,
+  RED_B_R = 4    // vector slot entry 0 and the scalar slot
+};
+constexpr int kRedLocalMax = 16;  // sets up to this size stay in the serial CTA
+
+__device__ __forceinline__ int red_count(int set, int q) {
+  switch (set) {
+    case RED_M_G: return 2 * q * q;
+    case RED_H_S: return q * q + q;
+    case RED_S: return q;
+    case RED_SCALAR: return 1;
+    default: return 2;
+  }
+}
+
+__device__ __forceinline__ int red_slot(int set, int q, int e) {
+  const int sq = q * q;
+  switch (set) {
+    case RED_M_G: {
+      const int f = e < sq ? e : e - sq;
+      const int a = f / q;
+      return (e < sq ? kSlotGram0 : kSlotGram1) + a * kMaxP + (f - a * q);
+    }
+    case RED_H_S: {
+      if (e >= sq) return kSlotVec + (e - sq);
+      const int a = e / q;
+      return kSlotGram0 + a * kMaxP + (e - a * q);
+    }
+    case RED_S: return kSlotVec + e;
+    case RED_SCALAR: return kSlotScalar;
+    default: return e == 0 ? kSlotVec : kSlotScalar;
+  }
+}
+
+__device__ __forceinline__ double warp_sum_parts(const Params& prm, int off) {
   const int G = grp_size(prm);
-  int g = 0;
-  // blocks of 8 CTAs: 16 independent loads in flight, summed in CTA order
-  for (; g + 8 <= G; g += 8) {
+  const int lane = threadIdx.x & 31;
+  DSum t{0.0, 0.0};
+  int g0 = 0;
+  // up to 8 partials per lane with all loads in flight, then summed in order
+  for (; g0 < G; g0 += 8 * 32) {
     double h[8], l[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const double* pp = prm.part + (size_t)(g + q) * kPartStride;
-      h[q] = ldcg(pp + off);
-      l[q] = ldcg(pp + kPartHalf + off);
+    for (int k = 0; k < 8; ++k) {
+      const int g = g0 + lane + 32 * k;
+      const double* pp = prm.part + (size_t)g * kPartStride;
+      h[k] = g < G ? ldcg(pp + off) : 0.0;
+      l[k] = g < G ? ldcg(pp + kPartHalf + off) : 0.0;
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) dsum_add(t, h[q], l[q]);
+    for (int k = 0; k < 8; ++k)
+      if (g0 + lane + 32 * k < G) dsum_add(t, h[k], l[k]);
   }
-  for (; g < G; ++g) {
-    const double* q = prm.part + (size_t)g * kPartStride;
-    dsum_add(t, ldcg(q + off), ldcg(q + kPartHalf + off));
-  }
+  t = dsum_warp(t);
   return __dadd_rn(t.hi, t.lo);
 }
 
-// Y <- L^{-T} L^{-1} Y for m right-hand sides (thread per column), L lower.
-__device__ void chol_solve_cols(const double* l, double* y, int m) {
-  const int c = threadIdx.x;
-  if (c < m) {
-    for (int a = 0; a < m; ++a) {
-      double v = y[a * kLd + c];
-      for (int u = 0; u < a; ++u) v -= l[a * kLd + u] * y[u * kLd + c];
-      y[a * kLd + c] = v / l[a * kLd + a];
+// Entries w0 + j * wstride (j = 0, 1, ...) of the set, one per warp of this CTA.
+__device__ void reduce_entries(const Params& prm, int set, int q, int w0, int wstride) {
+  const int E = red_count(set, q);
+  for (int e = w0 + (int)(threadIdx.x >> 5); e < E; e += wstride) {
+    const int off = red_slot(set, q, e);
+    const double v = warp_sum_parts(prm, off);
+    if ((threadIdx.x & 31) == 0) prm.st->red[off] = v;
+  }
+}
+
+__device__ __forceinline__ double red_get(const DevState* st, int off) {
+  return ldcg(&st->red[off]);
+}
+
+// Y <- L^{-T} L^{-1} Y for the m columns of y, L lower (m x m, m <= NB).
+// One warp per right-hand side: lane a holds entry a of the column in a
+// register; each solved entry is broadcast by a shuffle and applied to the
+// remaining rows at once, so the dependent chain per row is a shuffle, a
+// multiplication by the pivot reciprocal and an FMA.  rinv: shared scratch
+// for the m pivot reciprocals.
+template <int NB>
+__device__ void chol_solve_cols(const double* l, double* y, int m, double* rinv) {
+  const int lane = threadIdx.x & 31;
+  if ((int)threadIdx.x < m) rinv[threadIdx.x] = 1.0 / l[threadIdx.x * kLd + threadIdx.x];
+  __syncthreads();
+  for (int c = threadIdx.x >> 5; c < m; c += kWarps) {  // warp-uniform
+    double v = lane < m ? y[lane * kLd + c] : 0.0;
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      if (u < m) {
+        const double yu = __shfl_sync(0xffffffffu, v, u) * rinv[u];
+        const double lau = (lane > u && lane < m) ? l[lane * kLd + u] : 0.0;
+        v = (lane == u) ? yu : (lane > u ? fma(-lau, yu, v) : v);
+      }
     }
-    for (int a = m - 1; a >= 0; --a) {
-      double v = y[a * kLd + c];
-      for (int u = a + 1; u < m; ++u) v -= l[u * kLd + a] * y[u * kLd + c];
-      y[a * kLd + c] = v / l[a * kLd + a];
+#pragma unroll
+    for (int u = NB - 1; u >= 0; --u) {
+      if (u < m) {
+        const double yu = __shfl_sync(0xffffffffu, v, u) * rinv[u];
+        const double lua = (lane < u) ? l[u * kLd + lane] : 0.0;
+        v = (lane == u) ? yu : (lane < u ? fma(-lua, yu, v) : v);
+      }
     }
+    if (lane < m) y[lane * kLd + c] = v;
   }
   __syncthreads();
 }
@@ -553,19 +678,24 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // replacement steps: sets s, jbest, relres_recur and the next ctrl.
 __device__ void stop_test(const Params& prm, SerialSmem& S, int pk, int where) {
   DevState* st = prm.st;
+  if (threadIdx.x < pk) {
+    const double s = sqrt(S.s2[threadIdx.x]);
+    S.sv[threadIdx.x] = s;
+    st->s[threadIdx.x] = s;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     bool bad = false;
     int jmin = 0;
     for (int j = 0; j < pk; ++j) {
-      const double s = sqrt(S.s2[j]);
-      st->s[j] = s;
+      const double s = S.sv[j];
       if (!finite(s)) bad = true;
-      if (j > 0 && s < sqrt(S.s2[jmin])) jmin = j;
+      if (j > 0 && s < S.sv[jmin]) jmin = j;
     }
     if (bad) {
       set_error(st, ST_ERR_NUMERICAL, where);
     } else {
-      const double smin = sqrt(S.s2[jmin]);
+      const double smin = S.sv[jmin];
       const double bn = ldcg(&st->bnorm);
       const bool stop = smin <= prm.tol * bn;
       st->jbest = jmin;
@@ -585,7 +715,58 @@ __device__ void stop_test(const Params& prm, SerialSmem& S, int pk, int where) {
   __syncthreads();
 }
 
+// Right-looking Cholesky of the unit-diagonal scaled M (lower triangle in
+// S.l) by one warp: lane i holds row i in registers, column j's multipliers
+// reach the other lanes by shuffles.  Columns are taken in agent order; a
+// column whose pivot is below rank_tol is skipped (agent dropped, Algorithm
+// 3), a pivot below -sqrt(rank_tol) means A is not SPD.  Leaves the factor in
+// S.l, the kept columns in S.keep, their count in S.chol_m and 0 / 2 (not
+// SPD) / 3 (NaN) in S.chol_fail.  Called by warp 0 only.
+template <int NB>
+__device__ void warp_chol(const Params& prm, SerialSmem& S, int pk) {
+  const int lane = threadIdx.x & 31;
+  double r[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k)
+    r[k] = (lane < pk && k <= lane) ? S.l[lane * kLd + k] : 0.0;
+  const double neg_lim = -sqrt(prm.rank_tol);
+  int m = 0, fail = 0;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < pk && fail == 0) {
+      const double d = __shfl_sync(0xffffffffu, r[j], j);
+      int decision = 0;  // 0 keep, 1 drop, 2 not SPD, 3 NaN
+      if (S.m[j * kLd + j] == 0.0) decision = 1;  // zero direction
+      else if (!(d == d)) decision = 3;
+      else if (d < neg_lim) decision = 2;
+      else if (d < prm.rank_tol) decision = 1;
+      if (decision >= 2) {
+        fail = decision;
+      } else if (decision == 0) {
+        const double ljj = sqrt(d);
+        if (lane == j) r[j] = ljj;
+        else if (lane > j) r[j] = r[j] / ljj;
+#pragma unroll
+        for (int k = j + 1; k < NB; ++k) {
+          const double lkj = __shfl_sync(0xffffffffu, r[j], k);
+          if (lane >= k) r[k] -= r[j] * lkj;
+        }
+        if (lane == 0) S.keep[m] = j;
+        ++m;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NB; ++k)
+    if (lane < pk && k <= lane) S.l[lane * kLd + k] = r[k];
+  if (lane == 0) {
+    S.chol_m = m;
+    S.chol_fail = fail;
+  }
+}
+
 // alpha step: M, G -> rank test, factor, alpha_k^T (Algorithm 2 / 3).
+template <int NB>
 __device__ void serial_alpha(const Params& prm, SerialSmem& S) {
   DevState* st = prm.st;
   const int tid = threadIdx.x;
@@ -595,8 +776,7 @@ __device__ void serial_alpha(const Params& prm, SerialSmem& S) {
   for (int e = tid; e < 2 * sq; e += kThreads) {
     const int f = e < sq ? e : e - sq;
     const int a = f / pk, c = f - a * pk;
-    const int off = (e < sq ? kSlotGram0 : kSlotGram1) + a * kMaxP + c;
-    (e < sq ? S.m : S.g)[a * kLd + c] = sum_parts(prm, off);
+    (e < sq ? S.m : S.g)[a * kLd + c] = red_get(st, red_slot(RED_M_G, pk, e));
   }
   __syncthreads();
   // M <- (M + M^T) / 2
@@ -631,36 +811,13 @@ __device__ void serial_alpha(const Params& prm, SerialSmem& S) {
     else if (c == a) S.l[a * kLd + a] = 1.0;
   }
   __syncthreads();
-  // right-looking Cholesky, columns in agent order; a column whose pivot is
-  // below rank_tol is skipped (agent dropped, Algorithm 3)
-  const double neg_lim = -sqrt(prm.rank_tol);
-  int m = 0;
-  for (int j = 0; j < pk; ++j) {
-    const double d = S.l[j * kLd + j];
-    const bool zero_dir = S.m[j * kLd + j] == 0.0;
-    int decision = 0;  // 0 keep, 1 drop, 2 not SPD, 3 NaN
-    if (zero_dir) decision = 1;
-    else if (!(d == d)) decision = 3;
-    else if (d < neg_lim) decision = 2;
-    else if (d < prm.rank_tol) decision = 1;
-    if (decision >= 2) {
-      if (tid == 0) set_error(st, decision == 2 ? ST_ERR_NOT_SPD : ST_ERR_NUMERICAL, 2);
-      __syncthreads();
-      return;
-    }
-    if (decision == 1) continue;
-    const double ljj = sqrt(d);
+  if (tid < 32) warp_chol<NB>(prm, S, pk);
+  __syncthreads();
+  const int m = S.chol_m;
+  if (S.chol_fail) {
+    if (tid == 0) set_error(st, S.chol_fail == 2 ? ST_ERR_NOT_SPD : ST_ERR_NUMERICAL, 2);
     __syncthreads();
-    if (tid == 0) { S.l[j * kLd + j] = ljj; S.keep[m] = j; }
-    for (int i = j + 1 + tid; i < pk; i += kThreads) S.l[i * kLd + j] /= ljj;
-    __syncthreads();
-    const int nt = pk - j - 1;
-    for (int e = tid; e < nt * nt; e += kThreads) {
-      const int ii = j + 1 + e / nt, ll = j + 1 + e % nt;
-      if (ll <= ii) S.l[ii * kLd + ll] -= S.l[ii * kLd + j] * S.l[ll * kLd + j];
-    }
-    ++m;
-    __syncthreads();
+    return;
   }
   if (m == 0) {
     if (tid == 0) set_error(st, ST_ERR_NUMERICAL, 3);
@@ -682,7 +839,7 @@ __device__ void serial_alpha(const Params& prm, SerialSmem& S) {
     S.l[a * kLd + c] = S.sc[S.keep[a]] * S.g[S.keep[c] * kLd + S.keep[a]];
   }
   __syncthreads();
-  chol_solve_cols(S.m, S.l, m);
+  chol_solve_cols<NB>(S.m, S.l, m, S.sv);
   for (int e = tid; e < m * m; e += kThreads) {
     const int b = e / m, a = e - b * m;
     const double v = -S.sc[S.keep[b]] * S.l[b * kLd + a];
@@ -717,6 +874,7 @@ __device__ void serial_alpha(const Params& prm, SerialSmem& S) {
 }
 
 // beta step: H, s2 -> beta_k^T, iteration count, stop test.
+template <int NB>
 __device__ void serial_beta(const Params& prm, SerialSmem& S) {
   DevState* st = prm.st;
   const int tid = threadIdx.x;
@@ -726,9 +884,9 @@ __device__ void serial_beta(const Params& prm, SerialSmem& S) {
   for (int e = tid; e < sq + pk; e += kThreads) {
     if (e < sq) {
       const int a = e / pk, c = e - a * pk;
-      S.g[a * kLd + c] = sum_parts(prm, kSlotGram0 + a * kMaxP + c);
+      S.g[a * kLd + c] = red_get(st, kSlotGram0 + a * kMaxP + c);
     } else {
-      S.s2[e - sq] = sum_parts(prm, kSlotVec + (e - sq));
+      S.s2[e - sq] = red_get(st, kSlotVec + (e - sq));
     }
   }
   for (int e = tid; e < sq; e += kThreads) {
@@ -748,7 +906,7 @@ __device__ void serial_beta(const Params& prm, SerialSmem& S) {
     __syncthreads();
     return;
   }
-  chol_solve_cols(S.m, S.l, pk);
+  chol_solve_cols<NB>(S.m, S.l, pk, S.sv);
   for (int e = tid; e < sq; e += kThreads) {
     const int b = e / pk, a = e - b * pk;
     const double v = -S.sc[b] * S.l[b * kLd + a];
@@ -768,7 +926,7 @@ __device__ void serial_beta(const Params& prm, SerialSmem& S) {
 __device__ void serial_bnorm(const Params& prm, SerialSmem& S) {
   DevState* st = prm.st;
   if (threadIdx.x == 0) {
-    const double b2 = sum_parts(prm, kSlotScalar);
+    const double b2 = red_get(st, kSlotScalar);
     const double bn = sqrt(b2);
     st->bnorm = bn;
     if (!finite(bn)) {
@@ -789,7 +947,7 @@ __device__ void serial_bnorm(const Params& prm, SerialSmem& S) {
 __device__ void serial_norms(const Params& prm, SerialSmem& S, bool replacement) {
   DevState* st = prm.st;
   const int pk = ldcg(&st->pk);
-  for (int e = threadIdx.x; e < pk; e += kThreads) S.s2[e] = sum_parts(prm, kSlotVec + e);
+  for (int e = threadIdx.x; e < pk; e += kThreads) S.s2[e] = red_get(st, kSlotVec + e);
   if (threadIdx.x == 0 && replacement) {
     st->replacements = ldcg(&st->replacements) + 1;
     st->k_replaced = ldcg(&st->k);
@@ -801,7 +959,7 @@ __device__ void serial_norms(const Params& prm, SerialSmem& S, bool replacement)
 __device__ void serial_check(const Params& prm) {
   DevState* st = prm.st;
   if (threadIdx.x == 0) {
-    const double tr = sqrt(sum_parts(prm, kSlotScalar)) / ldcg(&st->bnorm);
+    const double tr = sqrt(red_get(st, kSlotScalar)) / ldcg(&st->bnorm);
     st->relres_true = tr;
     if (!finite(tr)) {
       set_error(st, ST_ERR_NUMERICAL, 11);
@@ -826,8 +984,7 @@ __device__ void serial_block_product(const Params& prm, SerialSmem& S) {
   for (int e = threadIdx.x; e < 2 * sq; e += kThreads) {
     const int f = e < sq ? e : e - sq;
     const int a = f / q, c = f - a * q;
-    const int off = (e < sq ? kSlotGram0 : kSlotGram1) + a * kMaxP + c;
-    (e < sq ? S.m : S.g)[a * kLd + c] = sum_parts(prm, off);
+    (e < sq ? S.m : S.g)[a * kLd + c] = red_get(st, red_slot(RED_M_G, q, e));
   }
   __syncthreads();
   for (int e = threadIdx.x; e < sq; e += kThreads) {
@@ -861,8 +1018,8 @@ __device__ void serial_sigma(const Params& prm, int pk) {
 __device__ void serial_refine(const Params& prm) {
   DevState* st = prm.st;
   if (threadIdx.x == 0) {
-    const double bn = sqrt(sum_parts(prm, kSlotVec));
-    const double rn = sqrt(sum_parts(prm, kSlotScalar));
+    const double bn = sqrt(red_get(st, kSlotVec));
+    const double rn = sqrt(red_get(st, kSlotScalar));
     st->bnorm = bn;
     st->rnorm = rn;
     st->relres_true = bn > 0.0 ? rn / bn : rn;
@@ -1172,6 +1329,68 @@ __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, 
 }
 
 // --------------------------------------------------------------------------
+// FP32 A-pass of the batched refinement's inner solves (policy POL_F32):
+// Y = A32 V (- b 1^T) with A32 the FP32 copy of A (rows padded with zeros to
+// a32_ld, a multiple of 4).  The operand columns are first written as FP32
+// rows (own rows, then a barrier).  Each warp then takes whole rows: lane l
+// multiplies the elements 4l + 128s of the row (16-byte loads) with the
+// operand rows, and a butterfly over the lanes sums each column.  Products
+// and sums are FP32 on the FP32 pipe: the inner solve needs only the
+// accuracy of its FP32 operator, and the FP32 rate is 64 times the FP64 rate
+// on GB300.  The operand rows are read through L1, which is coherent with
+// this CTA's own writes: the policy runs in groups of one CTA only.
+// --------------------------------------------------------------------------
+template <int P>
+__device__ bool apass_f32(const Params& prm, const double* V, int pk, double* Y, bool sub_b,
+                          int64_t r0, int64_t r1, SyncShared* ss, int* s_err) {
+  const int p = prm.p;
+  const int64_t ld = prm.a32_ld;
+  float* vt = prm.vt32;
+  const int tid = threadIdx.x;
+  const int64_t nr = r1 - r0;
+  for (int64_t idx = tid; idx < nr * P; idx += kThreads) {
+    const int c = (int)(idx / nr);
+    const int64_t i = r0 + (idx - (int64_t)c * nr);
+    vt[c * ld + i] = c < pk ? (float)ldcg(V + i * p + c) : 0.f;
+  }
+  if (!grid_barrier(prm, ss, s_err)) return false;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int64_t w0 = r0 + (nr * warp) / kWarps;
+  const int64_t w1 = r0 + (nr * (warp + 1)) / kWarps;
+  for (int64_t row = w0; row < w1; ++row) {
+    const float* Ar = prm.a32 + row * ld;
+    float acc[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) acc[c] = 0.f;
+    for (int64_t k = 4 * lane; k < ld; k += 128) {
+      const float4 a = __ldcg(reinterpret_cast<const float4*>(Ar + k));
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        const float4 v = *reinterpret_cast<const float4*>(vt + c * ld + k);
+        acc[c] = fmaf(a.x, v.x, acc[c]);
+        acc[c] = fmaf(a.y, v.y, acc[c]);
+        acc[c] = fmaf(a.z, v.z, acc[c]);
+        acc[c] = fmaf(a.w, v.w, acc[c]);
+      }
+    }
+    float mine = 0.f;
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], m);
+      if (lane == c) mine = acc[c];
+    }
+    if (lane < pk) {
+      double y = (double)mine;
+      if (sub_b) y -= prm.b[row];
+      Y[row * p + lane] = y;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// --------------------------------------------------------------------------
 // The persistent kernel.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ double splitmix_uniform(unsigned long long seed,
@@ -1201,17 +1420,30 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
   const int p = prm.p;
   double* mypart = prm.part + (size_t)cta * kPartStride;
 
-#define CCG_SYNC_SERIAL(CALL)              \
-  {                                        \
-    const int f_ = grid_arrive(prm, &ss);  \
-    if (f_ < 0) return;                    \
-    if (f_ == 1) {                         \
-      if (!cta_error(st, &s_err)) {        \
-        CALL;                              \
-      }                                    \
-      grid_release(prm, &ss);              \
-    }                                      \
-    if (cta_error(st, &s_err)) return;     \
+  // Exchange point: the group's sums of the reduction set SET (size from Q)
+  // land in st->red, then the last-arriving CTA runs CALL and releases the
+  // others.  Large sets are summed by all CTAs after an extra grid barrier.
+#define CCG_SYNC_RED(SET, Q, CALL)                                           \
+  {                                                                          \
+    const int q_ = (Q);                                                      \
+    const bool spread_ = G > 1 && red_count(SET, q_) > kRedLocalMax;         \
+    if (spread_) {                                                           \
+      if (!grid_barrier(prm, &ss, &s_err)) return;                           \
+      reduce_entries(prm, SET, q_, cta * kWarps, G * kWarps);                \
+    }                                                                        \
+    const int f_ = grid_arrive(prm, &ss);                                    \
+    if (f_ < 0) return;                                                      \
+    if (f_ == 1) {                                                           \
+      if (!cta_error(st, &s_err)) {                                          \
+        if (!spread_) {                                                      \
+          reduce_entries(prm, SET, q_, 0, kWarps);                           \
+          __syncthreads();                                                   \
+        }                                                                    \
+        CALL;                                                                \
+      }                                                                      \
+      grid_release(prm, &ss);                                                \
+    }                                                                        \
+    if (cta_error(st, &s_err)) return;                                       \
   }
 
   if (prm.mode == MODE_BARRIER_SELFTEST) {
@@ -1223,9 +1455,9 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     if (prm.mode == MODE_BLOCK_PRODUCT) {
       const int q = prm.q;
       apass<P, VEC>(prm, prm.V, q, 0, q, prm.Wout, q, false, r0, r1, smem);
-      partial_grams(prm.V, prm.Wout, prm.U, prm.U ? prm.V : nullptr, nullptr, q, q, r0, r1,
+      partial_grams<true>(prm.V, prm.Wout, prm.U, prm.U ? prm.V : nullptr, nullptr, q, q, r0, r1,
                     mypart);
-      CCG_SYNC_SERIAL(serial_block_product(prm, S));
+      CCG_SYNC_RED(RED_M_G, q, serial_block_product(prm, S));
       return;
     }
     if (prm.mode == MODE_REFINE) {
@@ -1238,19 +1470,21 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       partial_sumsq(prm.ref_r, 1, r0, r1, mypart, kSlotScalar);
       __syncthreads();
       partial_sumsq(prm.b, 1, r0, r1, mypart, kSlotVec);
-      CCG_SYNC_SERIAL(serial_refine(prm));
+      CCG_SYNC_RED(RED_B_R, 1, serial_refine(prm));
       const double rn = ldcg(&st->rnorm);
       const double scale = rn > 0.0 ? sqrt((double)n) / rn : 0.0;
       for (int64_t i = r0 + tid; i < r1; i += kThreads) prm.ref_bin[i] = -ldcg(prm.ref_r + i) * scale;
       return;
     }
   } else {
-    if (prm.mode == MODE_BLOCK_PRODUCT) {
-      // W = A_lp V on the tensor cores (same code as the inner solves' A-pass)
-      if (lp_apass<P, POL>(prm, prm.V, prm.q, prm.Wout, false, r0, r1, *L, &ss, &s_err) &&
-          tid == 0 && cta == 0)
-        st->result = ST_OK;
-      return;
+    if constexpr (POL != POL_F32) {
+      if (prm.mode == MODE_BLOCK_PRODUCT) {
+        // W = A_lp V on the tensor cores (same code as the inner solves' A-pass)
+        if (lp_apass<P, POL>(prm, prm.V, prm.q, prm.Wout, false, r0, r1, *L, &ss, &s_err) &&
+            tid == 0 && cta == 0)
+          st->result = ST_OK;
+        return;
+      }
     }
     if (prm.mode != MODE_SOLVE || !prm.skip_true_check) {
       if (tid == 0 && cta == 0) set_error(st, ST_ERR_INVALID, 14);
@@ -1278,7 +1512,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     prm.X[idx] = v;
   }
   partial_sumsq(prm.b, 1, r0, r1, mypart);
-  CCG_SYNC_SERIAL(serial_bnorm(prm, S));
+  CCG_SYNC_RED(RED_SCALAR, 1, serial_bnorm(prm, S));
 
   if (tid == 0) s_int[0] = ldcg(&st->ctrl);
   __syncthreads();
@@ -1286,12 +1520,14 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     // R_0 = A X_0 - b 1^T ; D_0 = R_0
     if constexpr (POL == POL_FP64) {
       apass<P, VEC>(prm, prm.X, p, 0, p, prm.R, p, true, r0, r1, smem);
+    } else if constexpr (POL == POL_F32) {
+      if (!apass_f32<P>(prm, prm.X, p, prm.R, true, r0, r1, &ss, &s_err)) return;
     } else {
       if (!lp_apass<P, POL>(prm, prm.X, p, prm.R, true, r0, r1, *L, &ss, &s_err)) return;
     }
     for (int64_t idx = r0 * p + tid; idx < r1 * p; idx += kThreads) prm.D0[idx] = ldcg(prm.R + idx);
-    partial_grams(nullptr, nullptr, nullptr, nullptr, prm.R, p, p, r0, r1, mypart);
-    CCG_SYNC_SERIAL(serial_norms(prm, S, false));
+    partial_grams<POL == POL_FP64>(nullptr, nullptr, nullptr, nullptr, prm.R, p, p, r0, r1, mypart);
+    CCG_SYNC_RED(RED_S, p, serial_norms(prm, S, false));
   }
 
   int cur = 0;
@@ -1335,7 +1571,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       if constexpr (POL == POL_FP64) {
         apass<1, VEC>(prm, prm.X, p, jb, 1, prm.W, p, true, r0, r1, smem);
         partial_sumsq(prm.W, p, r0, r1, mypart);
-        CCG_SYNC_SERIAL(serial_check(prm));
+        CCG_SYNC_RED(RED_SCALAR, 1, serial_check(prm));
       }
       continue;
     }
@@ -1346,19 +1582,21 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         const int c = (int)(idx % p);
         if (c < pk) D[idx] = ldcg(prm.R + idx);
       }
-      partial_grams(nullptr, nullptr, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
-      CCG_SYNC_SERIAL(serial_norms(prm, S, true));
+      partial_grams<POL == POL_FP64>(nullptr, nullptr, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
+      CCG_SYNC_RED(RED_S, pk, serial_norms(prm, S, true));
       continue;
     }
 
     // ---- one cCG iteration ----
     if constexpr (POL == POL_FP64) {
       apass<P, VEC>(prm, D, p, 0, pk, prm.W, p, false, r0, r1, smem);
+    } else if constexpr (POL == POL_F32) {
+      if (!apass_f32<P>(prm, D, pk, prm.W, false, r0, r1, &ss, &s_err)) return;
     } else {
       if (!lp_apass<P, POL>(prm, D, pk, prm.W, false, r0, r1, *L, &ss, &s_err)) return;
     }
-    partial_grams(D, prm.W, prm.R, D, nullptr, p, pk, r0, r1, mypart);
-    CCG_SYNC_SERIAL(serial_alpha(prm, S));
+    partial_grams<POL == POL_FP64>(D, prm.W, prm.R, D, nullptr, p, pk, r0, r1, mypart);
+    CCG_SYNC_RED(RED_M_G, pk, serial_alpha<P>(prm, S));
 
     if (tid == 0) {
       s_int[2] = ldcg(&st->changed);
@@ -1393,7 +1631,8 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     }
     pk = s_int[1];
 
-    // X += D alpha^T ; R += W alpha^T
+    // X += D alpha^T ; R += W alpha^T (or, explicit residual, R = A X - b 1^T
+    // after a grid barrier: every CTA's rows of X are needed)
     {
       double* Ts = smem;
       for (int e = tid; e < pk * pk; e += kThreads) {
@@ -1401,6 +1640,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         Ts[b * kLd + a] = ldcg(&st->alphaT[b * kMaxP + a]);
       }
       __syncthreads();
+      const bool rec = !prm.explicit_residual;
       const int64_t cnt = (r1 - r0) * pk;
       for (int64_t idx = tid; idx < cnt; idx += kThreads) {
         const int64_t i = r0 + idx / pk;
@@ -1410,15 +1650,21 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         for (int b = 0; b < pk; ++b) {
           const double t = Ts[b * kLd + a];
           dx = fma(ldcg(D + i * p + b), t, dx);
-          dr = fma(ldcg(prm.W + i * p + b), t, dr);
+          if (rec) dr = fma(ldcg(prm.W + i * p + b), t, dr);
         }
         prm.X[i * p + a] += dx;
-        prm.R[i * p + a] += dr;
+        if (rec) prm.R[i * p + a] += dr;
       }
       __syncthreads();
+      if constexpr (POL == POL_FP64) {
+        if (!rec) {
+          if (!grid_barrier(prm, &ss, &s_err)) return;
+          apass<P, VEC>(prm, prm.X, p, 0, pk, prm.R, p, true, r0, r1, smem);
+        }
+      }
     }
-    partial_grams(prm.R, prm.W, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
-    CCG_SYNC_SERIAL(serial_beta(prm, S));
+    partial_grams<POL == POL_FP64>(prm.R, prm.W, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
+    CCG_SYNC_RED(RED_H_S, pk, serial_beta<P>(prm, S));
 
     if (tid == 0) s_int[0] = ldcg(&st->ctrl);
     __syncthreads();
@@ -1443,7 +1689,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       cur ^= 1;
     }
   }
-#undef CCG_SYNC_SERIAL
+#undef CCG_SYNC_RED
 }
 
 
@@ -1532,6 +1778,60 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_kernel(const __grid_constant
 // Batched solver: each CTA repeatedly takes the next system from the queue
 // (largest first, as ordered by the host) and solves it alone -- the solver
 // body with a group of one CTA, whose barriers are CTA barriers.
+// Out-of-line copies of the solve body for the batched kernels: the batched
+// refinement kernel runs two policies, and separate calls keep each one's
+// register allocation its own.
+template <int P, bool VEC, int POL>
+__device__ __noinline__ void solve_call(const Params& prm, double* smem) {
+  solve_body<P, VEC, POL>(prm, smem, nullptr);
+}
+
+// Fresh solver state for one system of a batch (thread 0).
+__device__ void reset_state(DevState* st, int p) {
+  st->bar_count = 0;
+  st->bar_gen = 0;
+  st->error = 0;
+  st->result = 0;
+  st->ctrl = 0;
+  st->k = 0;
+  st->pk = p;
+  st->prev_pk = p;
+  st->changed = 0;
+  st->jbest = 0;
+  st->replacements = 0;
+  st->drops = 0;
+  st->k_replaced = -1;
+  st->zero_rhs = 0;
+  st->relres_true = 0.0;
+  for (int j = 0; j < kMaxP; ++j) st->agent[j] = j;
+}
+
+// Per-system parameters of a batched solve (thread 0; q in shared memory).
+__device__ void batch_params(const Params& prm, Params& q, long long i, size_t slot) {
+  const int64_t* d = prm.batch_desc + 4 * i;  // n, A offset, vector offset, index
+  q = prm;
+  q.n = d[0];
+  q.lda = d[0] + (d[0] & 1);
+  q.A = prm.A + d[1];
+  q.b = prm.b + d[2];
+  q.x_out = prm.x_out + d[2];
+  double* w = prm.X + slot * (size_t)prm.batch_slot_stride;
+  const size_t blk = (size_t)prm.batch_slot_stride / 5;
+  q.X = w;
+  q.R = w + blk;
+  q.D0 = w + 2 * blk;
+  q.D1 = w + 3 * blk;
+  q.W = w + 4 * blk;
+  q.part = prm.part + slot * kPartStride;
+  q.st = prm.st + slot;
+  q.expected_ctas = 1u;
+  q.group_ctas = 1;
+  q.group_rank = 0;
+}
+
+// Batched solver: each CTA takes systems from a queue (largest first) and
+// solves them one at a time as a group of one CTA (grid barriers become CTA
+// barriers).
 template <int P>
 __global__ void __launch_bounds__(kThreads, 1) batch_kernel(const __grid_constant__ Params prm) {
   extern __shared__ __align__(1024) uint8_t dyn_smem[];
@@ -1545,42 +1845,8 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(const __grid_constan
     const long long i = s_sys;
     if (i >= prm.batch_count) break;
     if (tid == 0) {
-      const int64_t* d = prm.batch_desc + 4 * i;  // n, A offset, vector offset, index
-      q = prm;
-      q.n = d[0];
-      q.lda = d[0] + (d[0] & 1);
-      q.A = prm.A + d[1];
-      q.b = prm.b + d[2];
-      q.x_out = prm.x_out + d[2];
-      double* w = prm.X + slot * (size_t)prm.batch_slot_stride;
-      const size_t blk = (size_t)prm.batch_slot_stride / 5;
-      q.X = w;
-      q.R = w + blk;
-      q.D0 = w + 2 * blk;
-      q.D1 = w + 3 * blk;
-      q.W = w + 4 * blk;
-      q.part = prm.part + slot * kPartStride;
-      q.st = prm.st + slot;
-      q.expected_ctas = 1u;
-      q.group_ctas = 1;
-      q.group_rank = 0;
-      DevState* st = q.st;
-      st->bar_count = 0;
-      st->bar_gen = 0;
-      st->error = 0;
-      st->result = 0;
-      st->ctrl = 0;
-      st->k = 0;
-      st->pk = prm.p;
-      st->prev_pk = prm.p;
-      st->changed = 0;
-      st->jbest = 0;
-      st->replacements = 0;
-      st->drops = 0;
-      st->k_replaced = -1;
-      st->zero_rhs = 0;
-      st->relres_true = 0.0;
-      for (int j = 0; j < kMaxP; ++j) st->agent[j] = j;
+      batch_params(prm, q, i, slot);
+      reset_state(q.st, prm.p);
       __threadfence();
     }
     __syncthreads();
@@ -1593,6 +1859,148 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(const __grid_constan
       prm.batch_status[idx] = err != 0 ? err : *(volatile const int*)&st->result;
       prm.batch_iters[idx] = *(volatile const int*)&st->k;
       prm.batch_relres[idx] = *(volatile const double*)&st->relres_true;
+    }
+    __syncthreads();
+  }
+}
+
+// Batched mixed-precision solver: per system, an FP32 copy of A, then FP64
+// iterative refinement (x += d; r = b - A x in FP64) around inner cCG solves
+// on the FP32 copy (A-pass on the FP32 pipe), all inside one launch.  The
+// refinement ends when the true relative residual reaches tol, when two
+// steps in a row fail to reduce it, after batch_max_outer steps, or when the
+// inner solve breaks down; the best x is returned.
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1) batch_ir_kernel(const __grid_constant__ Params prm) {
+  extern __shared__ __align__(1024) uint8_t dyn_smem[];
+  __shared__ Params q;
+  __shared__ long long s_sys;
+  double* smem = reinterpret_cast<double*>(dyn_smem);
+  const int tid = threadIdx.x;
+  const size_t slot = blockIdx.x;
+  for (;;) {
+    if (tid == 0) s_sys = (long long)atomicAdd(prm.batch_next, 1u);
+    __syncthreads();
+    const long long i = s_sys;
+    if (i >= prm.batch_count) break;
+    if (tid == 0) {
+      batch_params(prm, q, i, slot);
+      double* v = prm.batch_vec + slot * (size_t)prm.batch_vec_stride;
+      const int64_t n = q.n;
+      q.ref_x = q.x_out;
+      q.ref_r = v;
+      q.ref_bin = v + n;
+      q.ref_delta = nullptr;
+      q.ref_coef = 0.0;
+      q.a32_ld = (n + 3) & ~int64_t(3);
+      float* f = prm.batch_f32 + slot * (size_t)prm.batch_f32_stride;
+      q.a32 = f;
+      q.vt32 = f + n * q.a32_ld;
+    }
+    __syncthreads();
+    const int64_t n = q.n;
+    const int64_t ld = q.a32_ld;
+    double* xs = q.x_out;
+    double* delta = q.ref_bin + n;
+    double* xbest = delta + n;
+    const double* bsys = q.b;
+    {
+      // FP32 copy of A (zero padding to ld), zero operand padding, x = 0
+      float* a32 = const_cast<float*>(q.a32);
+      for (int64_t idx = tid; idx < n * ld; idx += kThreads) {
+        const int64_t r = idx / ld, c = idx - r * ld;
+        a32[idx] = c < n ? (float)q.A[r * q.lda + c] : 0.f;
+      }
+      for (int64_t idx = tid; idx < (int64_t)P * (ld - n); idx += kThreads) {
+        const int64_t c = idx / (ld - n), k = n + (idx - c * (ld - n));
+        q.vt32[c * ld + k] = 0.f;
+      }
+      for (int64_t r = tid; r < n; r += kThreads) xs[r] = 0.0;
+    }
+    // r = b - A x, norms
+    if (tid == 0) {
+      reset_state(q.st, 1);
+      q.mode = MODE_REFINE;
+      q.p = 1;
+      __threadfence();
+    }
+    __syncthreads();
+    solve_call<P, false, POL_FP64>(q, smem);
+    __syncthreads();
+    const DevState* st = q.st;
+    int err = ldcg(&st->error);
+    double rnorm = ldcg(&st->rnorm);
+    double relres = ldcg(&st->relres_true);
+    const double bnorm = ldcg(&st->bnorm);
+    double best = relres;
+    for (int64_t r = tid; r < n; r += kThreads) xbest[r] = xs[r];
+    int status = (err != 0) ? err : ((bnorm == 0.0 || relres <= prm.tol) ? ST_OK : ST_NOT_CONVERGED);
+    int total = 0, outer = 0, stall = 0;
+    while (status == ST_NOT_CONVERGED && outer < prm.batch_max_outer && total < prm.maxit) {
+      ++outer;
+      __syncthreads();
+      if (tid == 0) {
+        // inner solve A32 d = b_in (unit-RMS right-hand side), recurrence stop
+        reset_state(q.st, prm.p);
+        q.mode = MODE_SOLVE;
+        q.p = prm.p;
+        q.b = q.ref_bin;
+        q.x_out = delta;
+        q.skip_true_check = 1;
+        q.replacement = 0;
+        q.tol = fmax(prm.batch_inner_tol, 0.5 * prm.tol / relres);
+        q.maxit = prm.maxit - total;
+        __threadfence();
+      }
+      __syncthreads();
+      solve_call<P, false, POL_F32>(q, smem);
+      __syncthreads();
+      err = ldcg(&st->error);
+      if (err == ST_ERR_NOT_SPD || err == ST_ERR_NUMERICAL) break;  // inner breakdown
+      if (err != 0) {
+        status = err;
+        break;
+      }
+      total += ldcg(&st->k);
+      // x += d ||r|| / sqrt(n) ; r = b - A x (FP64)
+      __syncthreads();
+      if (tid == 0) {
+        reset_state(q.st, 1);
+        q.mode = MODE_REFINE;
+        q.p = 1;
+        q.b = bsys;
+        q.x_out = xs;
+        q.ref_delta = delta;
+        q.ref_coef = rnorm / sqrt((double)n);
+        __threadfence();
+      }
+      __syncthreads();
+      solve_call<P, false, POL_FP64>(q, smem);
+      __syncthreads();
+      err = ldcg(&st->error);
+      if (err != 0) {
+        status = err;
+        break;
+      }
+      rnorm = ldcg(&st->rnorm);
+      relres = ldcg(&st->relres_true);
+      if (relres < best) {
+        best = relres;
+        stall = 0;
+        for (int64_t r = tid; r < n; r += kThreads) xbest[r] = xs[r];
+      } else if (++stall >= 2) {
+        break;
+      }
+      if (best <= prm.tol) status = ST_OK;
+    }
+    __syncthreads();
+    for (int64_t r = tid; r < n; r += kThreads) xs[r] = xbest[r];
+    if (tid == 0) {
+      const int64_t idx = prm.batch_desc[4 * i + 3];
+      prm.batch_status[idx] = (status == ST_NOT_CONVERGED && best <= prm.tol) ? ST_OK : status;
+      prm.batch_iters[idx] = total;
+      prm.batch_relres[idx] = best;
+      if (prm.batch_outer) prm.batch_outer[idx] = outer;
     }
     __syncthreads();
   }

@@ -78,3 +78,41 @@ def test_batched_empty_and_invalid(env):
         assert summ.status == 0
         summ, *_ = s.solve_batched([1], z, z, z, p=2, tol=1e-8, maxit=10)  # p > n
         assert summ.status == -1
+
+
+@pytest.mark.parametrize("p", [1, 4])
+def test_batched_fp32_refinement_reaches_fp64_accuracy(env, p):
+    """Batched FP32 + FP64 refinement: every system reaches the FP64 target
+    (true relative residual <= 1e-10, checked here in NumPy) and its x agrees
+    with the FP64 oracle to the accuracy the residual implies."""
+    torch, ccg, oracle = env["torch"], env["ccg"], env["oracle"]
+    rng = np.random.default_rng(10 + p)
+    sizes = [int(v) for v in np.round(np.exp(rng.uniform(np.log(8), np.log(400), 120)))]
+    sizes = [max(s, p) for s in sizes] + [p, 401, 33]
+    mats, rhs = make_batch(sizes, seed=20 + p)
+    dA, db, v_off = pack(ccg, torch, sizes, mats, rhs)
+    x = torch.zeros_like(db)
+    with ccg.Solver(precision=ccg.FP32_IR) as s:
+        summ, st, it, rr = s.solve_batched(sizes, dA, db, x, p=p, tol=1e-10, maxit=10000)
+    assert summ.status == 0, summ
+    assert 1 <= summ.outer_steps <= 30
+    xs = x.cpu().numpy()
+    for k, (n, A, b) in enumerate(zip(sizes, mats, rhs)):
+        xi = xs[v_off[k]:v_off[k] + n]
+        assert st[k] == 0, (k, n, st[k], rr[k])
+        relres = np.linalg.norm(b - A @ xi) / np.linalg.norm(b)
+        assert relres <= 1.01e-10 and abs(relres - rr[k]) <= 1e-12, (k, relres, rr[k])
+        if k % 10 == 0:
+            X0 = oracle.initial_block(n, p, None, 1.0, 0)
+            ref = oracle.ccg(A, b, X0, 1e-10, 10000)
+            cond = np.linalg.cond(A)
+            err = np.linalg.norm(xi - ref["x"]) / np.linalg.norm(ref["x"])
+            assert err <= 4.0 * cond * 1e-10, (k, n, err, cond)
+
+
+def test_batched_rejects_tensor_core_precisions(env):
+    torch, ccg = env["torch"], env["ccg"]
+    z = torch.zeros(16, dtype=torch.float64, device="cuda")
+    with ccg.Solver(precision=ccg.BF16_IR) as s:
+        summ, *_ = s.solve_batched([2], z, z, z, p=1, tol=1e-8, maxit=10)
+        assert summ.status == -1

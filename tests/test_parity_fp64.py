@@ -247,3 +247,26 @@ def test_full_size_exp_kernel_n8192_p8(env):
     launch configuration the benchmark times, against the oracle."""
     A, b = wl.exp_kernel(8192, seed=1, length=0.2, nugget=1e-2)
     check_against_oracle(env, A, b, 8, maxit=5000)
+
+
+@pytest.mark.parametrize("n,p", [(64, 3), (257, 8), (1031, 7), (2048, 16)])
+def test_explicit_residual_against_oracle(env, n, p):
+    """Algorithm 2 as printed: R_{k+1} = A X_{k+1} - b 1^T each iteration."""
+    torch = env["torch"]
+    A, b = wl.random_spd(n, seed=n * 5 + p, cond=300.0)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda:0")
+    with env["ccg"].Solver(device=0, explicit_residual=True) as s:
+        r = s.solve(dev(env, A), dev(env, b), x, p=p, tol=TOL, maxit=20 * n)
+    torch.cuda.synchronize()
+    X0 = env["oracle"].initial_block(n, p, None, 1.0, 0)
+    ref = env["oracle"].ccg(A, b, X0, TOL, 20 * n, nthreads=8, explicit_residual=True)
+    assert ref["status"] == 0 and r.status == 0, (ref["status_name"], r)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(A @ xg - b) / np.linalg.norm(b) <= TOL * 1.01
+    assert np.linalg.norm(xg - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
+    assert abs(r.iterations - ref["iterations"]) <= 2, (r.iterations, ref["iterations"])
+
+
+def test_explicit_residual_rejected_with_mixed_precision(env):
+    with pytest.raises(RuntimeError):
+        env["ccg"].Solver(device=0, explicit_residual=True, precision=env["ccg"].FP32_IR)
