@@ -34,6 +34,11 @@ WORKLOAD = ("plain FP64 cCG: A = exp(-|z_i-z_j|/0.2) + 1e-2 I on n=8192 points U
             "(seed 1), b ~ N(0,1), x0 = 0, tol 1e-10 relative")
 METRIC = "solves/s at relres 1e-10 (FP64 cCG)"
 GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+# DRAM bytes (read + write) per pass over A of the persistent FP64 solve kernel,
+# measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a
+# 20-iteration solve of the benchmark system: 22 passes, 11 853.2 MB.  The
+# traffic grows with the passes, so a full solve is scaled from it.
+NCU_BYTES_PER_PASS = {(8192, 8): (11816769792 + 36412928) / 22.0}
 
 
 def parse():
@@ -56,6 +61,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision lines")
     ap.add_argument("--lowp-n", type=int, default=32768,
                     help="size of the tensor-core block-product measurement")
+    ap.add_argument("--lowp-fmt", default="bf16", choices=["bf16", "fp8"],
+                    help="storage format of A for --profile lowp")
     return ap.parse_args()
 
 
@@ -263,6 +270,13 @@ def mixed_lines(ccg, dev, stream, A, b, p, steps, tol=TOL):
     return out
 
 
+def sliced_sweep(ccg, stream, dA, db, x, n, ps=(1, 4, 8, 16)):
+    """FP64 cCG with the block product formed exactly from FP8 slices of A and
+    D on the tensor cores (CCG_FP64_SLICED), on the benchmark system."""
+    with ccg.Solver(stream=stream.cuda_stream, precision=ccg.FP64_SLICED) as s:
+        return p_sweep(ccg, s, stream, dA, db, x, n, ps)
+
+
 def p_sweep(ccg, solver, stream, dA, db, x, n, ps=(1, 4, 8, 16, 32)):
     """FP64 cCG on the benchmark system for every agent count of the sweep:
     one warm-up and one timed solve each."""
@@ -300,8 +314,9 @@ def precision_lines(ccg, stream, A, p=16, tol=TOL, seed=2):
     out = {"workload": f"exponential kernel, n = {n} points U[0,1]^3 (seed {seed}), length 0.1, "
                        f"nugget 1e-3, b ~ N(0,1), p = {p}, tol {tol}", "n": n, "p": p}
     x64 = None
-    for name, prec, reps in [("fp64", ccg.FP64, 1), ("fp32_ir", ccg.FP32_IR, 2),
-                             ("bf16_ir", ccg.BF16_IR, 1), ("fp8_ir", ccg.FP8_IR, 1)]:
+    for name, prec, reps in [("fp64", ccg.FP64, 1), ("fp64_sliced", ccg.FP64_SLICED, 2),
+                             ("fp32_ir", ccg.FP32_IR, 2), ("bf16_ir", ccg.BF16_IR, 1),
+                             ("fp8_ir", ccg.FP8_IR, 1)]:
         x = torch.zeros(n, dtype=torch.float64, device=dev)
         with ccg.Solver(stream=stream.cuda_stream, precision=prec,
                         max_outer=0 if prec in (ccg.FP64, ccg.FP32_IR) else 12) as s:
@@ -325,7 +340,7 @@ def precision_lines(ccg, stream, A, p=16, tol=TOL, seed=2):
             line["err_vs_fp64"] = float(torch.linalg.vector_norm(x - x64) /
                                         torch.linalg.vector_norm(x64))
         out[name] = line
-    for k in ("fp32_ir", "bf16_ir", "fp8_ir"):
+    for k in ("fp64_sliced", "fp32_ir", "bf16_ir", "fp8_ir"):
         out[f"speedup_{k}_vs_fp64"] = (out[k]["solves_per_s"] / out["fp64"]["solves_per_s"]
                                        if out[k]["status"] == "CCG_OK" else None)
     return out
@@ -497,7 +512,9 @@ def main():
         return
     if args.profile == "lowp":
         A32 = device_exp_kernel(args.lowp_n, 2, 0.1, 1e-3, dev)
-        m = solver.lowp_matrix(A32, ccg.LOWP_BF16)
+        m = solver.lowp_matrix(A32, ccg.LOWP_BF16 if args.lowp_fmt == "bf16" else ccg.LOWP_FP8_E4M3)
+        del A32
+        torch.cuda.empty_cache()
         V = torch.randn(args.lowp_n, p, dtype=torch.float64, device=dev)
         W = torch.empty(args.lowp_n, p, dtype=torch.float64, device=dev)
         for _ in range(args.warmup + args.steps):
@@ -506,7 +523,7 @@ def main():
         torch.cuda.synchronize()
         m.close()
         solver.close()
-        print(json.dumps({"profile": "lowp", "n": args.lowp_n, "p": p}))
+        print(json.dumps({"profile": "lowp", "fmt": args.lowp_fmt, "n": args.lowp_n, "p": p}))
         return
     if args.profile != "none":
         # profiling driver: the launches ncu captures, nothing else timed
@@ -591,11 +608,12 @@ def main():
                "h2d_bytes_per_step": int(A.nbytes + b.nbytes),
                "d2h_bytes_per_step": int(8 * n + 192)}
 
-    mixed = lowp = batched = serving = sweep = precision = None
+    mixed = lowp = batched = serving = sweep = sweep_sliced = precision = None
     if rank == 0 and not args.no_mixed:
         from paper_1204_0069_gb300 import workloads as wl
         peaks0 = measured_peaks()
         sweep = p_sweep(ccg, solver, stream, dA, db, x, n)
+        sweep_sliced = sliced_sweep(ccg, stream, dA, db, x, n)
         A3 = device_exp_kernel(args.lowp_n, 2, 0.1, 1e-3, dev)
         lowp = lowp_roofline(ccg, solver, dev, A3, 16, peaks0.get("hbm_gbs"))
         precision = precision_lines(ccg, stream, A3, p=16)
@@ -627,6 +645,9 @@ def main():
         peaks = measured_peaks()
         fp64_peak = 1.25  # TFLOP/s: nominal GB300 FP64 rate (no measured FP64 figure)
         achieved = fl / (kms / 1e3) / 1e12
+        per_pass = NCU_BYTES_PER_PASS.get((n, p))
+        traffic = (per_pass * (1 + r0.iterations + checks + r0.replacements)
+                   if per_pass is not None else None)
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -639,7 +660,9 @@ def main():
             "latency_ms": {"p50": float(np.percentile(kernel_ms, 50)),
                            "p99": float(np.percentile(kernel_ms, 99))},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
+                         "traffic_note": ("DRAM bytes per launch, scaled from an ncu capture "
+                                          "of a 20-iteration solve (bytes per pass x passes)"),
                          "kernel": f"fp64_kernel<{p_bucket(p)},true> (persistent solve)",
                          "peak_note": "nominal FP64 rate (FP64 pipe bound)"},
             "apass": {"ms": bp_ms, "gbs": 8.0 * n * n / (bp_ms / 1e3) / 1e9,
@@ -651,6 +674,8 @@ def main():
         }
         if sweep is not None:
             line["p_sweep"] = sweep
+        if sweep_sliced is not None:
+            line["p_sweep_fp64_sliced"] = sweep_sliced
         if lowp is not None:
             line["lowp_apass"] = lowp
         if precision is not None:

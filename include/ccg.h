@@ -60,7 +60,19 @@ typedef enum {
     CCG_FP32_IR = 1,         /* A in FP32, products from TF32 halves on the
                                 tensor cores, FP64 refinement                 */
     CCG_BF16_IR = 2,         /* A in BF16 on the tensor cores, FP64 refinement */
-    CCG_FP8_IR = 3           /* A in FP8 E4M3 on the tensor cores, FP64 refinement */
+    CCG_FP8_IR = 3,          /* A in FP8 E4M3 on the tensor cores, FP64 refinement */
+    CCG_FP64_SLICED = 4      /* FP64 cCG (Algorithm 2, FP64 everywhere) whose block
+                                products A D_k are formed on the FP8 tensor cores
+                                from an error-free split of A and D_k into 14
+                                slices of 4-bit integers each (the splitting of
+                                Ozaki, Ogita, Oishi and Rump, Numer. Algorithms
+                                59, 2012): every slice product is exact, the
+                                slices are combined in FP64, and the truncation
+                                error is below 2^-56 of each row's and column's
+                                largest entry.  The sliced copy of A (14 bytes per
+                                entry) is made in each call; p <= 16.  Rows of A
+                                and columns of D_k must have their largest
+                                magnitude in [2^-125, 2^127]                   */
 } ccg_precision;
 
 typedef struct {
@@ -76,7 +88,7 @@ typedef struct {
     double barrier_timeout_ms;  /* in-kernel barrier wait limit; 10000 ms    */
     int max_ctas;               /* 0 = one CTA per SM; else an upper bound   */
     double inner_tol;           /* mixed precision: relative tolerance of each
-                                   inner solve; 0 = 1e-4 (FP32), 1e-2 (BF16),
+                                   inner solve; 0 = 1e-3 (FP32), 1e-2 (BF16),
                                    1e-1 (FP8)                                 */
     int max_outer;              /* mixed precision: refinement steps; 0 = 60 */
     int explicit_residual;      /* 1: form R_{k+1} = A X_{k+1} - b 1' by a second
@@ -178,10 +190,14 @@ typedef enum {
     CCG_LOWP_BF16 = 0,      /* bfloat16, round to nearest (2 bytes/entry)      */
     CCG_LOWP_FP8_E4M3 = 1,  /* FP8 E4M3, one FP32 scale per row: A_ij ~= s_i q_ij,
                                s_i = max_j |A_ij| / 448 (1 byte/entry)        */
-    CCG_LOWP_FP32 = 2       /* FP32 (4 bytes/entry); the tensor cores form
+    CCG_LOWP_FP32 = 2,      /* FP32 (4 bytes/entry); the tensor cores form
                                (A_hi + A_lo)(D_hi + D_lo) from TF32 halves
                                (A_lo = A - tf32(A)), about 2^-21 relative
                                error per product                              */
+    CCG_LOWP_FP64_SLICED = 3 /* A_ij = 2^e_i sum_{s<14} q_s 16^-(s+1) with
+                               integers q_s in [-15, 15] stored as FP8 E4M3
+                               (14 bytes/entry, see CCG_FP64_SLICED); the
+                               block product is FP64-accurate; q <= 16        */
 } ccg_lowp_format;
 
 /* Opaque quantised matrix (device memory owned by the object). */

@@ -25,9 +25,9 @@ EXPORTED = ["ccg_config_init", "ccg_create", "ccg_destroy", "ccg_solve", "ccg_so
             "ccg_lowp_destroy", "ccg_solve_noalloc", "ccg_solve_mixed", "ccg_solve_batched",
             "ccg_server_config_init", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
             "ccg_server_stats", "ccg_server_destroy"]
-FP64, FP32_IR, BF16_IR, FP8_IR = 0, 1, 2, 3
+FP64, FP32_IR, BF16_IR, FP8_IR, FP64_SLICED = 0, 1, 2, 3, 4
 NOALLOC_MAX_NP = 131072
-LOWP_BF16, LOWP_FP8_E4M3, LOWP_FP32 = 0, 1, 2
+LOWP_BF16, LOWP_FP8_E4M3, LOWP_FP32, LOWP_FP64_SLICED = 0, 1, 2, 3
 
 
 class Config(ctypes.Structure):

@@ -13,6 +13,7 @@
 #include "ccg.h"
 #include "ccg_handle.h"
 #include "ccg_internal.h"
+#include "ccg_lowp.h"
 
 using ccg::DevState;
 using ccg::Params;
@@ -25,6 +26,21 @@ int grid_size(const ccg_handle_s* h, int64_t n) {
   int64_t g = std::min<int64_t>(h->num_sms, (n + ccg::kWarps - 1) / ccg::kWarps);
   if (h->cfg.max_ctas > 0) g = std::min<int64_t>(g, h->cfg.max_ctas);
   return (int)std::max<int64_t>(1, g);
+}
+
+// Stream-ordered buffers of one sliced FP64 solve (freed after the launch is
+// queued: the pool reuses them only after it completes).
+void release_aligned_copy(ccg_handle_s* h) {
+  if (h->aligned_copy) cudaFreeAsync(h->aligned_copy, h->stream);
+  h->aligned_copy = nullptr;
+}
+void release_sliced(ccg_handle_s* h, ccg_lowp_matrix_s* m) {
+  if (m) lowp_destroy_async(h, m);
+  if (h->sliced_dq) cudaFreeAsync(h->sliced_dq, h->stream);
+  if (h->sliced_part) cudaFreeAsync(h->sliced_part, h->stream);
+  h->sliced_dq = nullptr;
+  h->sliced_part = nullptr;
+  release_aligned_copy(h);
 }
 
 void init_state(DevState* s, int p) {
@@ -56,6 +72,7 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
     return st;
   };
   if (!h || n < 1 || p < 1 || p > ccg::kMaxP || p > n || lda < n || !(tol > 0.0) ||
+      (h->cfg.precision == CCG_FP64_SLICED && p > 16) ||
       !std::isfinite(tol) || maxit < 0 || !A || !b || !x_out)
     return fail(CCG_ERR_INVALID);
   DeviceGuard guard(h->device);
@@ -153,14 +170,78 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
   prm.expected_ctas = (unsigned)G;
 
   const int P = ccg::p_bucket(p);
-  const bool vec = (prm.lda % 2 == 0) && aligned(dA, 16);
-  if (ccg::fp64_ctas_per_sm(P, vec) < 1) return fail(CCG_ERR_CUDA);
+  bool vec = (prm.lda % 2 == 0) && aligned(dA, 16);
+  const bool sliced = h->cfg.precision == CCG_FP64_SLICED;
+  const int pol = sliced ? ccg::POL_SLICED : ccg::POL_FP64;
+  ccg_lowp_matrix_s* m = nullptr;
+  if (sliced) {
+    // FP64 cCG whose block products come from the FP8 slices of A on the
+    // tensor cores; the kernel's true-residual pass streams the FP64 A with
+    // 16-byte loads, so an unaligned A is copied with an even ld first
+    if (!vec) {
+      const int64_t ld2 = n + (n & 1);
+      double* t = nullptr;
+      e = cudaMallocAsync(reinterpret_cast<void**>(&t), (size_t)n * ld2 * sizeof(double), s);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(t, ld2 * sizeof(double), dA, prm.lda * sizeof(double),
+                              n * sizeof(double), n, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) {
+        if (t) cudaFreeAsync(t, s);
+        return fail(map_cuda(e));
+      }
+      h->aligned_copy = t;
+      prm.A = t;
+      prm.lda = ld2;
+      vec = true;
+    }
+    const int rc2 = lowp_create_async(h, CCG_LOWP_FP64_SLICED, n, prm.A, prm.lda, &m);
+    if (rc2 != CCG_OK) {
+      release_aligned_copy(h);
+      return fail(rc2);
+    }
+    const int NP = P;
+    const int NB = (ccg::lp::kSlicesHost * NP + 15) / 16 * 16;
+    const int64_t ldk = ccg::lp::ld_elems(n);
+    const int64_t T = (n + 127) / 128;
+    const size_t dq_bytes = (size_t)NB * ldk;
+    const size_t part_bytes = (size_t)(G + ccg::lp::kSlicesHost * T) * 128 * NP * sizeof(double);
+    void* dq = nullptr;
+    void* lpart = nullptr;
+    e = cudaMallocAsync(&dq, dq_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dq, 0, dq_bytes, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&lpart, part_bytes, s);
+    h->sliced_dq = dq;
+    h->sliced_part = lpart;
+    if (e != cudaSuccess) {
+      release_sliced(h, m);
+      return fail(map_cuda(e));
+    }
+    prm.lp_kelems = 128;
+    prm.lp_kc = (int)((n + 127) / 128);
+    prm.lp_tiles = T;
+    prm.lp_units = (int64_t)ccg::lp::kSlicesHost * T * prm.lp_kc;
+    prm.lp_row_scale = m->row_scale;
+    prm.lp_dq = dq;
+    prm.lp_ldk = ldk;
+    prm.lp_part = reinterpret_cast<float*>(lpart);
+    if (!ccg::lp::make_tensor_map(&prm.lp_tmA, m->q, ccg::lp::KIND_SLICED,
+                                  ccg::lp::kSlicesHost * ccg::lp::slice_rows(n), n, m->ldq, 128) ||
+        !ccg::lp::make_tensor_map(&prm.lp_tmB, dq, ccg::lp::KIND_SLICED, NB, n, ldk, NB)) {
+      release_sliced(h, m);
+      return fail(CCG_ERR_CUDA);
+    }
+  }
+  if (ccg::fp64_ctas_per_sm(P, vec, pol) < 1) {
+    release_sliced(h, m);
+    return fail(CCG_ERR_CUDA);
+  }
 
   init_state(h->h_state, p);
   e = cudaMemcpyAsync(prm.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev0, s);
-  if (e == cudaSuccess) e = ccg::launch_fp64(prm, P, vec, G, s);
+  if (e == cudaSuccess) e = ccg::launch_fp64(prm, P, vec, G, s, pol);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev1, s);
+  release_sliced(h, m);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->h_state, prm.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && !xo_dev)
@@ -218,7 +299,7 @@ int ccg_create(ccg_handle** out, const ccg_config* cfg) {
   else ccg_config_init(&c);
   if (!(c.rank_tol > 0.0) || !(c.barrier_timeout_ms > 0.0) ||
       (c.precision != CCG_FP64 && c.precision != CCG_FP32_IR && c.precision != CCG_BF16_IR &&
-       c.precision != CCG_FP8_IR) ||
+       c.precision != CCG_FP8_IR && c.precision != CCG_FP64_SLICED) ||
       c.max_ctas < 0 || c.inner_tol < 0.0 || c.max_outer < 0 ||
       (c.explicit_residual != 0 && c.explicit_residual != 1) ||
       (c.explicit_residual && c.precision != CCG_FP64))
@@ -265,7 +346,7 @@ int ccg_destroy(ccg_handle* h) {
 
 int ccg_solve(ccg_handle* h, int64_t n, const double* A, int64_t lda, const double* b,
               const double* x0, int p, double tol, int maxit, double* x_out, ccg_result* res) {
-  if (h && h->cfg.precision != CCG_FP64) {
+  if (h && h->cfg.precision != CCG_FP64 && h->cfg.precision != CCG_FP64_SLICED) {
     // mixed precision: quantise A into a copy for this solve, refine in FP64
     const int fmt = h->cfg.precision == CCG_BF16_IR   ? CCG_LOWP_BF16
                     : h->cfg.precision == CCG_FP32_IR ? CCG_LOWP_FP32

@@ -18,34 +18,49 @@ using namespace ccg_host;
 namespace {
 
 int lp_kind(int format) {
-  return format == CCG_LOWP_BF16 ? ccg::lp::KIND_BF16
-         : format == CCG_LOWP_FP32 ? ccg::lp::KIND_TF32X3
-                                   : ccg::lp::KIND_FP8;
+  return format == CCG_LOWP_BF16          ? ccg::lp::KIND_BF16
+         : format == CCG_LOWP_FP32        ? ccg::lp::KIND_TF32X3
+         : format == CCG_LOWP_FP64_SLICED ? ccg::lp::KIND_SLICED
+                                          : ccg::lp::KIND_FP8;
 }
 
 size_t lp_esize(int format) {
   return format == CCG_LOWP_BF16 ? 2 : format == CCG_LOWP_FP32 ? 4 : 1;
 }
 
+// Bytes of the entries of a quantised n x n matrix (sliced: all slices,
+// each padded to whole 128-row tiles).
+size_t lp_qbytes(int format, int64_t n, int64_t ldq) {
+  if (format == CCG_LOWP_FP64_SLICED)
+    return (size_t)ccg::lp::kSlicesHost * (size_t)ccg::lp::slice_rows(n) * (size_t)ldq;
+  return (size_t)n * (size_t)ldq * lp_esize(format);
+}
+
 // W = A_lp V through the persistent solver kernel's tensor-core A-pass (the
-// code path of the inner solves), used for the FP32 (TF32x3) format.
+// code path of the solves), used for the FP32 (TF32x3) and the sliced FP64
+// formats.
 int block_product_persistent(ccg_handle* h, const ccg_lowp_matrix_s* m, const double* dV, int q,
                              double* dW, float* device_ms) {
   const int64_t n = m->n;
   const int P = ccg::p_bucket(q);
-  const int NP = P <= 16 ? 16 : 32;
-  const int NB = 2 * NP;
+  const bool sliced = m->format == CCG_LOWP_FP64_SLICED;
+  const int NP = sliced ? P : P <= 16 ? 16 : 32;
+  const int NB = sliced ? (ccg::lp::kSlicesHost * NP + 15) / 16 * 16 : 2 * NP;
   const int64_t ldk = ccg::lp::ld_elems(n);
   const int64_t T = (n + 127) / 128;
-  const int pol = ccg::POL_TF32X3;
+  const int pol = sliced ? ccg::POL_SLICED : ccg::POL_TF32X3;
+  const int kind = sliced ? ccg::lp::KIND_SLICED : ccg::lp::KIND_TF32X3;
+  const size_t esz = sliced ? 1 : sizeof(float);
+  const int64_t tiles = sliced ? ccg::lp::kSlicesHost * T : T;
+  const size_t pesz = sliced ? sizeof(double) : sizeof(float);
   int64_t g = std::min<int64_t>(h->num_sms, (n + ccg::kWarps - 1) / ccg::kWarps);
   if (h->cfg.max_ctas > 0) g = std::min<int64_t>(g, h->cfg.max_ctas);
   const int G = (int)std::max<int64_t>(1, g);
   if (ccg::fp64_ctas_per_sm(P, true, pol) < 1) return CCG_ERR_CUDA;
   int rc = ensure(&h->ws, &h->ws_bytes,
                   Carve::need({(size_t)G * ccg::kPartStride * sizeof(double),
-                               sizeof(ccg::DevState), (size_t)NB * ldk * sizeof(float),
-                               (size_t)(G + T) * 128 * NP * sizeof(float)}));
+                               sizeof(ccg::DevState), (size_t)NB * ldk * esz,
+                               (size_t)(G + tiles) * 128 * NP * pesz}));
   if (rc != CCG_OK) return rc;
   Carve wc(h->ws);
   ccg::Params prm{};
@@ -53,8 +68,8 @@ int block_product_persistent(ccg_handle* h, const ccg_lowp_matrix_s* m, const do
   prm.lda = n;
   prm.part = wc.take<double>((size_t)G * ccg::kPartStride);
   prm.st = wc.take<ccg::DevState>(1);
-  prm.lp_dq = wc.take<float>((size_t)NB * ldk);
-  prm.lp_part = wc.take<float>((size_t)(G + T) * 128 * NP);
+  prm.lp_dq = wc.take<char>((size_t)NB * ldk * esz);
+  prm.lp_part = reinterpret_cast<float*>(wc.take<char>((size_t)(G + tiles) * 128 * NP * pesz));
   prm.mode = ccg::MODE_BLOCK_PRODUCT;
   prm.timeout_ns = (long long)(h->cfg.barrier_timeout_ms * 1e6);
   prm.expected_ctas = (unsigned)G;
@@ -62,17 +77,22 @@ int block_product_persistent(ccg_handle* h, const ccg_lowp_matrix_s* m, const do
   prm.Wout = dW;
   prm.q = q;
   prm.p = q;
-  prm.lp_kelems = 32;
-  prm.lp_kc = (int)((n + 31) / 32);
-  prm.lp_units = T * prm.lp_kc;
+  prm.lp_kelems = sliced ? 128 : 32;
+  prm.lp_kc = (int)((n + prm.lp_kelems - 1) / prm.lp_kelems);
+  prm.lp_tiles = T;
+  prm.lp_units = tiles * prm.lp_kc;
   prm.lp_ldk = ldk;
-  if (!ccg::lp::make_tensor_map(&prm.lp_tmA, m->q, ccg::lp::KIND_TF32X3, n, n, m->ldq, 128) ||
-      !ccg::lp::make_tensor_map(&prm.lp_tmB, prm.lp_dq, ccg::lp::KIND_TF32X3, NB, n, ldk, NB))
+  prm.lp_row_scale = m->row_scale;
+  const int64_t arows = sliced ? ccg::lp::kSlicesHost * ccg::lp::slice_rows(n) : n;
+  if (!ccg::lp::make_tensor_map(&prm.lp_tmA, m->q, kind, arows, n, m->ldq, 128) ||
+      !ccg::lp::make_tensor_map(&prm.lp_tmB, prm.lp_dq, kind, NB, n, ldk, NB))
     return CCG_ERR_CUDA;
   std::memset(h->h_state, 0, sizeof(ccg::DevState));
   h->h_state->pk = q;
   cudaStream_t s = h->stream;
-  cudaError_t e = cudaMemcpyAsync(prm.st, h->h_state, sizeof(ccg::DevState), cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemsetAsync(prm.lp_dq, 0, (size_t)NB * ldk * esz, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(prm.st, h->h_state, sizeof(ccg::DevState), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev0, s);
   if (e == cudaSuccess) e = ccg::launch_fp64(prm, P, true, G, s, pol);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev1, s);
@@ -100,9 +120,9 @@ int lowp_create_async(ccg_handle* h, int format, int64_t n, const double* A, int
   m->device = h->device;
   m->n = n;
   m->ldq = ccg::lp::ld_elems(n);
-  const size_t qbytes = (size_t)n * (size_t)m->ldq * lp_esize(format);
+  const size_t qbytes = lp_qbytes(format, n, m->ldq);
   cudaError_t e = cudaMallocAsync(&m->q, qbytes, s);
-  if (e == cudaSuccess && format == CCG_LOWP_FP8_E4M3)
+  if (e == cudaSuccess && (format == CCG_LOWP_FP8_E4M3 || format == CCG_LOWP_FP64_SLICED))
     e = cudaMallocAsync(reinterpret_cast<void**>(&m->row_scale), (size_t)n * sizeof(float), s);
   if (e == cudaSuccess) e = ccg::lp::quantize(lp_kind(format), A, lda, n, m->q, m->ldq, m->row_scale, s);
   if (e != cudaSuccess) {
@@ -130,7 +150,8 @@ int ccg_lowp_create(ccg_handle* h, int format, int64_t n, const double* A, int64
   if (!out) return CCG_ERR_INVALID;
   *out = nullptr;
   if (!h || !A || n < 1 || lda < n ||
-      (format != CCG_LOWP_BF16 && format != CCG_LOWP_FP8_E4M3 && format != CCG_LOWP_FP32) ||
+      (format != CCG_LOWP_BF16 && format != CCG_LOWP_FP8_E4M3 && format != CCG_LOWP_FP32 &&
+       format != CCG_LOWP_FP64_SLICED) ||
       !aligned(A, 8))
     return CCG_ERR_INVALID;
   DeviceGuard guard(h->device);
@@ -152,10 +173,9 @@ int ccg_lowp_create(ccg_handle* h, int format, int64_t n, const double* A, int64
   m->device = h->device;
   m->n = n;
   m->ldq = ccg::lp::ld_elems(n);
-  const size_t esz = lp_esize(format);
-  const size_t qbytes = (size_t)n * (size_t)m->ldq * esz;
+  const size_t qbytes = lp_qbytes(format, n, m->ldq);
   cudaError_t e = cudaMalloc(&m->q, qbytes);
-  if (e == cudaSuccess && format == CCG_LOWP_FP8_E4M3)
+  if (e == cudaSuccess && (format == CCG_LOWP_FP8_E4M3 || format == CCG_LOWP_FP64_SLICED))
     e = cudaMalloc(reinterpret_cast<void**>(&m->row_scale), (size_t)n * sizeof(float));
   if (e == cudaSuccess)
     e = ccg::lp::quantize(lp_kind(format), dA, ldA, n, m->q, m->ldq, m->row_scale, s);
@@ -216,7 +236,8 @@ int ccg_lowp_block_product(ccg_handle* h, const ccg_lowp_matrix* m, const double
   }
   if (!w_dev) dW = sc.take<double>(nq);
   if (e != cudaSuccess) return map_cuda(e);
-  if (m->format == CCG_LOWP_FP32) {
+  if (m->format == CCG_LOWP_FP32 || m->format == CCG_LOWP_FP64_SLICED) {
+    if (m->format == CCG_LOWP_FP64_SLICED && q > 16) return CCG_ERR_INVALID;
     int rc2 = block_product_persistent(h, m, dV, q, dW, device_ms);
     if (rc2 == CCG_OK && !w_dev) {
       e = cudaMemcpyAsync(W, dW, nq * sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -34,6 +34,10 @@ struct ccg_handle_s {
   ccg::DevState* h_state = nullptr;  // pinned host mirror of the device state
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   ccg_lowp_matrix_s* lp = nullptr;  // quantised copy made by ccg_solve (mixed precision)
+  // stream-ordered buffers of a sliced FP64 solve (live during one call)
+  void* sliced_dq = nullptr;
+  void* sliced_part = nullptr;
+  double* aligned_copy = nullptr;
 };
 
 namespace ccg_host {

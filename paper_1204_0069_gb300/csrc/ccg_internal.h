@@ -42,7 +42,10 @@ enum Mode : int {
 // quantised A on the tensor cores (inner solves of the mixed-precision path),
 // or an FP32 copy of A on the FP32 pipe (inner solves of the batched
 // mixed-precision path).
-enum Policy : int { POL_FP64 = 0, POL_BF16 = 1, POL_FP8 = 2, POL_TF32X3 = 3, POL_F32 = 4 };
+enum Policy : int {
+  POL_FP64 = 0, POL_BF16 = 1, POL_FP8 = 2, POL_TF32X3 = 3, POL_F32 = 4,
+  POL_SLICED = 5  // FP64 cCG with the block product formed exactly from FP8 slices
+};
 
 // Status values mirror ccg_status in include/ccg.h.
 enum Status : int {
@@ -154,7 +157,8 @@ struct Params {
   // tensor-core A-pass (policy != POL_FP64)
   int lp_kc;               // k-chunks per 128-row tile
   int lp_kelems;           // K elements per chunk
-  int64_t lp_units;        // row tiles x k-chunks
+  int64_t lp_units;        // row tiles x k-chunks (x slices for POL_SLICED)
+  int64_t lp_tiles;        // row tiles of one slice (POL_SLICED)
   const float* lp_row_scale;
   void* lp_dq;             // quantised operand rows (NB x lp_ldk)
   int64_t lp_ldk;

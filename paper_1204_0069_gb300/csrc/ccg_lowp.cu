@@ -279,6 +279,48 @@ __global__ void quant_fp8_kernel(const double* __restrict__ A, int64_t lda, int6
   }
 }
 
+// A (FP64) -> kSlices FP8 slices without rounding error (the error-free
+// splitting of Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and
+// its applications", Numer. Algorithms 59, 2012, with 4-bit slices).  With e_i
+// the binary exponent of the row's largest |A_ij| (so |A_ij| 2^-e_i < 1),
+// x = A_ij 2^-e_i is written as sum_s q_s 16^-(s+1) + r with integers
+// q_s = trunc(16 x_s) in [-15, 15] (x_0 = x, x_{s+1} = 16 x_s - q_s); every
+// step is exact in FP64 and the remainder |r| < 16^-kSlices is dropped.  The
+// q_s are exact in E4M3, so the tensor cores multiply slices exactly.  Slice
+// s of row i lands in row s * srows + i; scale[i] = 2^e_i.
+__global__ void slice_fp64_kernel(const double* __restrict__ A, int64_t lda, int64_t n,
+                                  uint8_t* __restrict__ Q, int64_t ldq, int64_t srows,
+                                  float* __restrict__ scale) {
+  __shared__ double red[32];
+  const int64_t i = blockIdx.x;
+  double m = 0.0;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) m = fmax(m, fabs(A[i * lda + k]));
+  for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) red[0] = m;
+  }
+  __syncthreads();
+  int e = 0;
+  if (red[0] > 0.0) frexp(red[0], &e);
+  if (threadIdx.x == 0) scale[i] = ldexpf(1.f, e);
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+    double x = ldexp(A[i * lda + k], -e);
+#pragma unroll
+    for (int sl = 0; sl < kSlices; ++sl) {
+      x *= 16.0;
+      const double q = trunc(x);
+      x -= q;
+      Q[((int64_t)sl * srows + i) * ldq + k] =
+          (uint8_t)__nv_cvt_double_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+    }
+  }
+}
+
 // Column max |V[:, j]| (for the FP8 column scales), as float bits.
 __global__ void colmax_kernel(const double* __restrict__ V, int64_t n, int q,
                               unsigned int* __restrict__ out) {
@@ -380,8 +422,20 @@ size_t part_floats(int64_t n, int ctas, int NP) {
   return (size_t)(ctas + T) * kBM * NP;
 }
 
+int64_t slice_rows(int64_t n) { return (n + kBM - 1) / kBM * kBM; }
+static_assert(kSlicesHost == kSlices, "slice count");
+
 cudaError_t quantize(int kind, const double* A, int64_t lda, int64_t n, void* Q, int64_t ldq,
                      float* row_scale, cudaStream_t s) {
+  if (kind == KIND_SLICED) {
+    // padding rows and columns of every slice stay zero
+    const int64_t srows = slice_rows(n);
+    cudaError_t e = cudaMemsetAsync(Q, 0, (size_t)kSlices * srows * ldq, s);
+    if (e != cudaSuccess) return e;
+    slice_fp64_kernel<<<(unsigned)n, 256, 0, s>>>(A, lda, n, reinterpret_cast<uint8_t*>(Q), ldq,
+                                                   srows, row_scale);
+    return cudaGetLastError();
+  }
   if (kind == KIND_BF16)
     quant_bf16_kernel<<<(unsigned)n, 256, 0, s>>>(A, lda, n, reinterpret_cast<__nv_bfloat16*>(Q), ldq);
   else if (kind == KIND_TF32X3)

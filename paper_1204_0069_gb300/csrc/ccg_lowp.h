@@ -9,7 +9,9 @@
 namespace ccg {
 namespace lp {
 
-enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1, KIND_TF32X3 = 2 };
+enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1, KIND_TF32X3 = 2, KIND_SLICED = 3 };
+// Slices of the sliced FP64 format (equal to the device-side kSlices).
+constexpr int kSlicesHost = 14;
 
 // Launch description of one stream-K block product.
 struct LpRun {
@@ -31,8 +33,12 @@ int64_t ld_elems(int64_t n);
 // Floats of partial-tile storage for a launch on `ctas` CTAs with N = NP.
 size_t part_floats(int64_t n, int ctas, int NP);
 // A (FP64) -> Q: BF16, FP8 E4M3 with per-row scales (row_scale, n floats), or FP32.
+// KIND_SLICED: kSlices FP8 slices stacked slice-major, each slice_rows() rows
+// of ldq bytes, with one power-of-two scale per row (row_scale).
 cudaError_t quantize(int kind, const double* A, int64_t lda, int64_t n, void* Q, int64_t ldq,
                      float* row_scale, cudaStream_t s);
+// Rows of one slice of the sliced FP64 format (n rounded up to 128).
+int64_t slice_rows(int64_t n);
 // V (FP64, n x q row-major) -> Vt: NP (BF16) or 2 NP (FP8 hi, lo) rows of ldk
 // elements, K contiguous; FP8 also writes the column scales (cmax: 32 uints).
 cudaError_t convert_operand(int kind, const double* V, int64_t n, int q, int NP, void* Vt,

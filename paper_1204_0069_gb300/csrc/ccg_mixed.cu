@@ -197,7 +197,7 @@ extern "C" int ccg_solve_mixed(ccg_handle* h, const ccg_lowp_matrix* m, int64_t 
       !ccg::lp::make_tensor_map(&in.lp_tmB, dq, kind, NB, n, ldk, NB))
     return fail(CCG_ERR_CUDA);
 
-  const double tin_default = fp8 ? 1e-1 : f32 ? 1e-4 : 1e-2;
+  const double tin_default = fp8 ? 1e-1 : f32 ? 1e-3 : 1e-2;
   const double tin = h->cfg.inner_tol > 0.0 ? h->cfg.inner_tol : tin_default;
   const int max_outer = h->cfg.max_outer > 0 ? h->cfg.max_outer : 60;
 

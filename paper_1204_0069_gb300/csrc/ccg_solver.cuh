@@ -156,14 +156,17 @@ __device__ int grid_arrive(const Params& prm, SyncShared* ss) {
     } else {
       flag = 0;
       const unsigned long long t0 = globaltimer_ns();
+      unsigned polls = 0;
+      // tight spin on the generation word (one thread per CTA); the error
+      // word and the time limit are looked at every 16th poll
       while (ld_acquire_u32(&st->bar_gen) == gen) {
+        if ((++polls & 15u) != 0u) continue;
         if (*(volatile int*)&st->error != 0) { flag = -1; break; }
         if (globaltimer_ns() - t0 > (unsigned long long)prm.timeout_ns) {
           set_error(st, ST_ERR_TIMEOUT, 100);
           flag = -1;
           break;
         }
-        __nanosleep(64);
       }
       __threadfence();
     }
@@ -194,11 +197,14 @@ __device__ __forceinline__ bool cta_error(const DevState* st, int* s_err) {
   return *s_err != 0;
 }
 
-// Plain barrier; false = leave the kernel.
+// Plain barrier; false = leave the kernel.  A released CTA has read the
+// error word after its wake-up (grid_arrive); only the releasing CTA reads it
+// again.
 __device__ bool grid_barrier(const Params& prm, SyncShared* ss, int* s_err) {
   const int f = grid_arrive(prm, ss);
   if (f < 0) return false;
-  if (f == 1) grid_release(prm, ss);
+  if (f == 0) return true;
+  grid_release(prm, ss);
   return !cta_error(prm.st, s_err);
 }
 
@@ -601,6 +607,9 @@ __device__ __forceinline__ int red_slot(int set, int q, int e) {
   }
 }
 
+// The butterfly skips the levels whose partner lanes hold no partial (G <= 16
+// leaves lanes >= G empty; adding their zeros is exact), so lane 0's sum is
+// the same as with all five levels.  The result is valid in lane 0.
 __device__ __forceinline__ double warp_sum_parts(const Params& prm, int off) {
   const int G = grp_size(prm);
   const int lane = threadIdx.x & 31;
@@ -620,7 +629,17 @@ __device__ __forceinline__ double warp_sum_parts(const Params& prm, int off) {
     for (int k = 0; k < 8; ++k)
       if (g0 + lane + 32 * k < G) dsum_add(t, h[k], l[k]);
   }
-  t = dsum_warp(t);
+  int top = 1;
+  while (top < G && top < 32) top <<= 1;
+  for (int m = top >> 1; m >= 1; m >>= 1) {
+    const double oh = __shfl_xor_sync(0xffffffffu, t.hi, m);
+    const double ol = __shfl_xor_sync(0xffffffffu, t.lo, m);
+    const bool low = (threadIdx.x & m) == 0;
+    DSum a = low ? t : DSum{oh, ol};
+    const DSum b = low ? DSum{oh, ol} : t;
+    dsum_add(a, b.hi, b.lo);
+    t = a;
+  }
   return __dadd_rn(t.hi, t.lo);
 }
 
@@ -743,6 +762,10 @@ __device__ void warp_chol(const Params& prm, SerialSmem& S, int pk) {
       if (decision >= 2) {
         fail = decision;
       } else if (decision == 0) {
+        // square root and division as in the textbook factorisation: the
+        // iteration count of an ill-conditioned solve follows the rounding of
+        // the factor (a reciprocal square root moved it by 9 of 388 at
+        // n = 8192, p = 8)
         const double ljj = sqrt(d);
         if (lane == j) r[j] = ljj;
         else if (lane > j) r[j] = r[j] / ljj;
@@ -1001,15 +1024,25 @@ __device__ void serial_block_product(const Params& prm, SerialSmem& S) {
 
 // FP8 operand: column scales sigma_j = max_i |V_ij| / 448 from the per-CTA
 // maxima in the vector slot (hi part).
-__device__ void serial_sigma(const Params& prm, int pk) {
+// Sliced FP64 operand (pow2): sigma_j = 2^e_j with e_j the binary exponent of
+// max_i |V_ij| (so |V_ij| / sigma_j < 1), from the same per-CTA maxima.
+__device__ void serial_sigma(const Params& prm, int pk, bool pow2 = false) {
   DevState* st = prm.st;
   if (threadIdx.x < pk) {
-    float m = 0.f;
+    double m = 0.0;
     const int G = gridDim.x;
     for (int g = 0; g < G; ++g)
-      m = fmaxf(m, (float)ldcg(prm.part + (size_t)g * kPartStride + kSlotVec + threadIdx.x));
-    st->sigma[threadIdx.x] = m > 0.f ? m / 448.f : 1.f;
-    if (!(m == m) || isinf(m)) set_error(st, ST_ERR_NUMERICAL, 12);
+      m = fmax(m, ldcg(prm.part + (size_t)g * kPartStride + kSlotVec + threadIdx.x));
+    if (pow2) {
+      int e = 0;
+      if (m > 0.0) frexp(m, &e);
+      st->sigma[threadIdx.x] = ldexpf(1.f, e);
+      if (!(m == m) || isinf(m) || e < -125 || e > 127) set_error(st, ST_ERR_NUMERICAL, 16);
+    } else {
+      const float mf = (float)m;
+      st->sigma[threadIdx.x] = mf > 0.f ? mf / 448.f : 1.f;
+      if (!(mf == mf) || isinf(mf)) set_error(st, ST_ERR_NUMERICAL, 12);
+    }
   }
   __syncthreads();
 }
@@ -1058,12 +1091,15 @@ template <int POL>
 struct LpCfg {
   static constexpr int KIND = (POL == POL_FP8)      ? tc::KIND_FP8
                               : (POL == POL_TF32X3) ? tc::KIND_TF32X3
+                              : (POL == POL_SLICED) ? tc::KIND_SLICED
                                                     : tc::KIND_BF16;
 };
 
-template <int P>
+// Operand columns of the tensor-core pass: 16 or 32 (the MMA's N), or P for
+// the sliced FP64 operand, whose kSlices slices per column fill N instead.
+template <int P, int POL>
 struct LpNP {
-  static constexpr int value = (P <= 16) ? 16 : 32;
+  static constexpr int value = (POL == POL_SLICED) ? P : (P <= 16) ? 16 : 32;
 };
 
 template <int KIND, int NP>
@@ -1223,16 +1259,41 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
         const int b = seg & 1;
         if (!tc::mbar_wait(tc::smem_u32(&accf[b]), ((uint32_t)seg >> 1) & 1u, to, err)) break;
         tc::fence_after();
-        float v[NM];
-        tc::tmem_ld<NM>(L.sh->tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * NM), v);
-        if constexpr (NM != NP) {
+        const uint32_t tbase = L.sh->tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * NM);
+        if constexpr (KIND == tc::KIND_SLICED) {
+          // accumulator column u NP + j holds the exact integer
+          // sum_k qA_s(row, k) qV_u(k, j); its weight is 16^-(s+u+2) (s: slice
+          // of A of this tile).  Combined in FP64, largest weight first.
+          const int sl = (int)(t / prm.lp_tiles);
+          double out[NP];
 #pragma unroll
-          for (int j = 0; j < NP; ++j) v[j] += v[NP + j];  // hi + lo halves
+          for (int j = 0; j < NP; ++j) out[j] = 0.0;
+#pragma unroll
+          for (int ch = 0; ch < NM / 16; ++ch) {
+            float v[16];
+            tc::tmem_ld<16>(tbase + (uint32_t)(ch * 16), v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const int col = ch * 16 + q;
+              const int u = col / NP;
+              if (u < tc::kSlices) out[col % NP] += ldexp((double)v[q], -4 * (sl + u + 2));
+            }
+          }
+          double* dst = reinterpret_cast<double*>(prm.lp_part) + ((size_t)(c + t) * tc::kBM + row) * NP;
+#pragma unroll
+          for (int j = 0; j < NP; ++j) dst[j] = out[j];
+        } else {
+          float v[NM];
+          tc::tmem_ld<NM>(tbase, v);
+          if constexpr (NM != NP) {
+#pragma unroll
+            for (int j = 0; j < NP; ++j) v[j] += v[NP + j];  // hi + lo halves
+          }
+          float* dst = prm.lp_part + ((size_t)(c + t) * tc::kBM + row) * NP;
+#pragma unroll
+          for (int j = 0; j < NP; j += 4)
+            *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
-        float* dst = prm.lp_part + ((size_t)(c + t) * tc::kBM + row) * NP;
-#pragma unroll
-        for (int j = 0; j < NP; j += 4)
-          *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         tc::fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(tc::smem_u32(&acce[b]));
@@ -1246,11 +1307,32 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
 
 // Y[:, 0:pk] = A_lp V[:, 0:pk] (- b) on the rows [r0, r1) of this CTA, with the
 // operand conversion, the tensor-core pass and the fixup.  false = leave.
+// Operand entry (column j of V, row i) in the MMA type: BF16, or the TF32
+// halves hi = tf32(v) (low 13 mantissa bits cleared) and lo = v - hi (exact
+// in FP32).  FP8 needs the column scales first and is converted in lp_apass.
+template <int KIND, int NP>
+__device__ __forceinline__ void lp_put(const Params& prm, int j, int64_t i, double v) {
+  const int64_t ldk = prm.lp_ldk;
+  if constexpr (KIND == tc::KIND_BF16) {
+    reinterpret_cast<__nv_bfloat16*>(prm.lp_dq)[(int64_t)j * ldk + i] = __double2bfloat16(v);
+  } else if constexpr (KIND == tc::KIND_TF32X3) {
+    const float f = (float)v;
+    const float hi = __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
+    float* o = reinterpret_cast<float*>(prm.lp_dq);
+    o[(int64_t)j * ldk + i] = hi;
+    o[(int64_t)(NP + j) * ldk + i] = f - hi;
+  }
+}
+
+// preconv: the operand rows already hold V in the MMA type (written by the
+// D-update, followed by a grid barrier), so the conversion and its barrier
+// are skipped.
 template <int P, int POL>
 __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, bool sub_b,
-                         int64_t r0, int64_t r1, LpCtx& L, SyncShared* ss, int* s_err) {
+                         int64_t r0, int64_t r1, LpCtx& L, SyncShared* ss, int* s_err,
+                         bool preconv = false) {
   constexpr int KIND = LpCfg<POL>::KIND;
-  constexpr int NP = LpNP<P>::value;
+  constexpr int NP = LpNP<P, POL>::value;
   DevState* st = prm.st;
   const int p = prm.p;
   const int tid = threadIdx.x;
@@ -1258,53 +1340,119 @@ __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, 
   const int64_t ldk = prm.lp_ldk;
   double* mypart = prm.part + (size_t)blockIdx.x * kPartStride;
 
-  if constexpr (KIND == tc::KIND_FP8) {
+  if constexpr (KIND == tc::KIND_FP8 || KIND == tc::KIND_SLICED) {
     for (int j = tid; j < pk; j += kThreads) {
-      float m = 0.f;
-      for (int64_t i = r0; i < r1; ++i) m = fmaxf(m, (float)fabs(ldcg(V + i * p + j)));
-      mypart[kSlotVec + j] = (double)m;
+      double m = 0.0;
+      for (int64_t i = r0; i < r1; ++i) m = fmax(m, fabs(ldcg(V + i * p + j)));
+      mypart[kSlotVec + j] = m;
     }
     const int f = grid_arrive(prm, ss);
     if (f < 0) return false;
     if (f == 1) {
-      if (!cta_error(st, s_err)) serial_sigma(prm, pk);
+      if (!cta_error(st, s_err)) serial_sigma(prm, pk, KIND == tc::KIND_SLICED);
       grid_release(prm, ss);
-    }
-    if (cta_error(st, s_err)) return false;
-  }
-  // operand row j (< NP) holds column j of V, zero beyond pk
-  for (int64_t idx = tid; idx < (int64_t)NP * nr; idx += kThreads) {
-    const int j = (int)(idx / nr);
-    const int64_t i = r0 + (idx - (int64_t)j * nr);
-    const double v = (j < pk) ? ldcg(V + i * p + j) : 0.0;
-    if constexpr (KIND == tc::KIND_BF16) {
-      reinterpret_cast<__nv_bfloat16*>(prm.lp_dq)[(int64_t)j * ldk + i] = __double2bfloat16(v);
-    } else if constexpr (KIND == tc::KIND_TF32X3) {
-      // hi = tf32(v) (low 13 mantissa bits cleared), lo = v - hi (exact in FP32)
-      const float f = (float)v;
-      const float hi = __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
-      float* o = reinterpret_cast<float*>(prm.lp_dq);
-      o[(int64_t)j * ldk + i] = hi;
-      o[(int64_t)(NP + j) * ldk + i] = f - hi;
-    } else {
-      const float sg = (j < pk) ? __ldcg(&st->sigma[j]) : 1.f;
-      const double x = v / (double)sg;
-      const __nv_fp8_storage_t h = __nv_cvt_double_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
-      const double hv = (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(h, __NV_E4M3)));
-      const __nv_fp8_storage_t l = __nv_cvt_double_to_fp8(x - hv, __NV_SATFINITE, __NV_E4M3);
-      uint8_t* o = reinterpret_cast<uint8_t*>(prm.lp_dq);
-      o[(int64_t)j * ldk + i] = (uint8_t)h;
-      o[(int64_t)(NP + j) * ldk + i] = (uint8_t)l;
+      if (cta_error(st, s_err)) return false;
     }
   }
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-  if (!grid_barrier(prm, ss, s_err)) return false;
+  if constexpr (KIND == tc::KIND_SLICED) {
+    // operand row u NP + j holds slice u of column j (x = V_ij / sigma_j,
+    // split as in the slicing of A); rows past kSlices NP stay zero
+    using Sh = tc::Shape<KIND, NP>;
+    uint8_t* o = reinterpret_cast<uint8_t*>(prm.lp_dq);
+    for (int64_t idx = tid; idx < (int64_t)NP * nr; idx += kThreads) {
+      const int j = (int)(idx / nr);
+      const int64_t i = r0 + (idx - (int64_t)j * nr);
+      double x = 0.0;
+      if (j < pk) {
+        const double v = ldcg(V + i * p + j);
+        int e;
+        frexpf(__ldcg(&st->sigma[j]), &e);  // sigma_j = 2^(e - 1)
+        x = ldexp(v, 1 - e);
+      }
+#pragma unroll
+      for (int u = 0; u < tc::kSlices; ++u) {
+        x *= 16.0;
+        const double q = trunc(x);
+        x -= q;
+        o[(int64_t)(u * NP + j) * ldk + i] =
+            (uint8_t)__nv_cvt_double_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+      }
+    }
+    for (int64_t idx = tid; idx < (int64_t)(Sh::NB - tc::kSlices * NP) * nr; idx += kThreads) {
+      const int64_t rrow = tc::kSlices * NP + idx / nr;
+      o[rrow * ldk + r0 + idx % nr] = 0;
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    if (!grid_barrier(prm, ss, s_err)) return false;
+  } else if (!preconv) {
+    // operand row j (< NP) holds column j of V, zero beyond pk
+    for (int64_t idx = tid; idx < (int64_t)NP * nr; idx += kThreads) {
+      const int j = (int)(idx / nr);
+      const int64_t i = r0 + (idx - (int64_t)j * nr);
+      const double v = (j < pk) ? ldcg(V + i * p + j) : 0.0;
+      if constexpr (KIND == tc::KIND_FP8) {
+        const float sg = (j < pk) ? __ldcg(&st->sigma[j]) : 1.f;
+        const double x = v / (double)sg;
+        const __nv_fp8_storage_t h = __nv_cvt_double_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+        const double hv = (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(h, __NV_E4M3)));
+        const __nv_fp8_storage_t l = __nv_cvt_double_to_fp8(x - hv, __NV_SATFINITE, __NV_E4M3);
+        uint8_t* o = reinterpret_cast<uint8_t*>(prm.lp_dq);
+        o[(int64_t)j * ldk + i] = (uint8_t)h;
+        o[(int64_t)(NP + j) * ldk + i] = (uint8_t)l;
+      } else {
+        lp_put<KIND, NP>(prm, j, i, v);
+      }
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    if (!grid_barrier(prm, ss, s_err)) return false;
+  }
   lp_pass<KIND, NP>(prm, L);
   if (!grid_barrier(prm, ss, s_err)) return false;
   // fixup: each owned row sums the partial tiles of the CTAs that covered it
   const int G = gridDim.x;
   const int64_t U = prm.lp_units;
   const int kc = prm.lp_kc;
+  if constexpr (KIND == tc::KIND_SLICED) {
+    // FP64 partial tiles, one per (slice of A, row tile) and CTA; the CTA
+    // range of each (slice, row tile) of this CTA's rows is found once
+    __shared__ int s_rng[4][tc::kSlices][2];
+    const int64_t Tp = prm.lp_tiles;
+    const int tr0 = (int)(r0 / tc::kBM);
+    const int ntr = (nr > 0) ? (int)((r1 - 1) / tc::kBM) - tr0 + 1 : 0;
+    for (int e = tid; e < ntr * tc::kSlices; e += kThreads) {
+      const int q = e / tc::kSlices, sl = e - q * tc::kSlices;
+      const int64_t t = (int64_t)sl * Tp + tr0 + q;
+      const int64_t lo = t * kc, hi = lo + kc;
+      int c0 = (int)((lo * G) / U);
+      while (c0 > 0 && tc::unit_begin(U, G, c0) > lo) --c0;
+      while (tc::unit_begin(U, G, c0 + 1) <= lo) ++c0;
+      int c1 = c0;
+      while (c1 + 1 < G && tc::unit_begin(U, G, c1 + 1) < hi) ++c1;
+      s_rng[q][sl][0] = c0;
+      s_rng[q][sl][1] = c1;
+    }
+    __syncthreads();
+    const double* part = reinterpret_cast<const double*>(prm.lp_part);
+    for (int64_t idx = tid; idx < nr * pk; idx += kThreads) {
+      const int64_t i = r0 + idx / pk;
+      const int j = (int)(idx - (idx / pk) * pk);
+      const int tr = (int)(i / tc::kBM);
+      const int rr = (int)(i - (int64_t)tr * tc::kBM);
+      double s = 0.0;
+      for (int sl = 0; sl < tc::kSlices; ++sl) {
+        const int64_t t = (int64_t)sl * Tp + tr;
+        for (int cc = s_rng[tr - tr0][sl][0]; cc <= s_rng[tr - tr0][sl][1]; ++cc) {
+          if (tc::unit_begin(U, G, cc + 1) <= tc::unit_begin(U, G, cc)) continue;
+          s += __ldcg(part + ((size_t)(cc + t) * tc::kBM + rr) * NP + j);
+        }
+      }
+      s *= (double)prm.lp_row_scale[i] * (double)__ldcg(&st->sigma[j]);
+      if (sub_b) s -= prm.b[i];
+      Y[i * p + j] = s;
+    }
+    __syncthreads();
+    return true;
+  } else {
   for (int64_t idx = tid; idx < nr * pk; idx += kThreads) {
     const int64_t i = r0 + idx / pk;
     const int j = (int)(idx - (idx / pk) * pk);
@@ -1326,6 +1474,7 @@ __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, 
   }
   __syncthreads();
   return true;
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -1442,8 +1591,8 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         CALL;                                                                \
       }                                                                      \
       grid_release(prm, &ss);                                                \
+      if (cta_error(st, &s_err)) return;                                     \
     }                                                                        \
-    if (cta_error(st, &s_err)) return;                                       \
   }
 
   if (prm.mode == MODE_BARRIER_SELFTEST) {
@@ -1486,7 +1635,8 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         return;
       }
     }
-    if (prm.mode != MODE_SOLVE || !prm.skip_true_check) {
+    // inner solves only, except the sliced FP64 policy: a full FP64 solve
+    if (prm.mode != MODE_SOLVE || (!prm.skip_true_check && POL != POL_SLICED)) {
       if (tid == 0 && cta == 0) set_error(st, ST_ERR_INVALID, 14);
       return;
     }
@@ -1526,11 +1676,15 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       if (!lp_apass<P, POL>(prm, prm.X, p, prm.R, true, r0, r1, *L, &ss, &s_err)) return;
     }
     for (int64_t idx = r0 * p + tid; idx < r1 * p; idx += kThreads) prm.D0[idx] = ldcg(prm.R + idx);
-    partial_grams<POL == POL_FP64>(nullptr, nullptr, nullptr, nullptr, prm.R, p, p, r0, r1, mypart);
+    partial_grams<POL == POL_FP64 || POL == POL_SLICED>(nullptr, nullptr, nullptr, nullptr, prm.R, p, p, r0, r1, mypart);
     CCG_SYNC_RED(RED_S, p, serial_norms(prm, S, false));
   }
 
   int cur = 0;
+  // BF16 / TF32 inner solves: the D-update writes D_{k+1} in the MMA type too,
+  // and the next tensor-core A-pass skips its conversion and barrier
+  constexpr bool kFuseConv = POL == POL_BF16 || POL == POL_TF32X3;
+  bool conv_ready = false;
   for (;;) {
     if (tid == 0) {
       s_int[0] = ldcg(&st->ctrl);
@@ -1558,7 +1712,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       return;
     }
 
-    if constexpr (POL != POL_FP64) {
+    if constexpr (POL != POL_FP64 && POL != POL_SLICED) {
       if (ctrl == CTRL_CHECK || ctrl == CTRL_REPLACE) {  // never reached by inner solves
         if (tid == 0) set_error(st, ST_ERR_INVALID, 15);
         return;
@@ -1568,7 +1722,8 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     if (ctrl == CTRL_CHECK) {
       // true residual of the best agent: W[:, 0] = A X e_jb - b
       const int jb = ldcg(&st->jbest);
-      if constexpr (POL == POL_FP64) {
+      if constexpr (POL == POL_FP64 || POL == POL_SLICED) {
+        // the FP64 true residual always runs on the FP64 pipe
         apass<1, VEC>(prm, prm.X, p, jb, 1, prm.W, p, true, r0, r1, smem);
         partial_sumsq(prm.W, p, r0, r1, mypart);
         CCG_SYNC_RED(RED_SCALAR, 1, serial_check(prm));
@@ -1577,12 +1732,16 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     }
 
     if (ctrl == CTRL_REPLACE) {
-      if constexpr (POL == POL_FP64) apass<P, VEC>(prm, prm.X, p, 0, pk, prm.R, p, true, r0, r1, smem);
+      if constexpr (POL == POL_FP64) {
+        apass<P, VEC>(prm, prm.X, p, 0, pk, prm.R, p, true, r0, r1, smem);
+      } else if constexpr (POL == POL_SLICED) {
+        if (!lp_apass<P, POL>(prm, prm.X, pk, prm.R, true, r0, r1, *L, &ss, &s_err)) return;
+      }
       for (int64_t idx = r0 * p + tid; idx < r1 * p; idx += kThreads) {
         const int c = (int)(idx % p);
         if (c < pk) D[idx] = ldcg(prm.R + idx);
       }
-      partial_grams<POL == POL_FP64>(nullptr, nullptr, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
+      partial_grams<POL == POL_FP64 || POL == POL_SLICED>(nullptr, nullptr, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
       CCG_SYNC_RED(RED_S, pk, serial_norms(prm, S, true));
       continue;
     }
@@ -1593,9 +1752,10 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     } else if constexpr (POL == POL_F32) {
       if (!apass_f32<P>(prm, D, pk, prm.W, false, r0, r1, &ss, &s_err)) return;
     } else {
-      if (!lp_apass<P, POL>(prm, D, pk, prm.W, false, r0, r1, *L, &ss, &s_err)) return;
+      if (!lp_apass<P, POL>(prm, D, pk, prm.W, false, r0, r1, *L, &ss, &s_err, conv_ready))
+        return;
     }
-    partial_grams<POL == POL_FP64>(D, prm.W, prm.R, D, nullptr, p, pk, r0, r1, mypart);
+    partial_grams<POL == POL_FP64 || POL == POL_SLICED>(D, prm.W, prm.R, D, nullptr, p, pk, r0, r1, mypart);
     CCG_SYNC_RED(RED_M_G, pk, serial_alpha<P>(prm, S));
 
     if (tid == 0) {
@@ -1663,7 +1823,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         }
       }
     }
-    partial_grams<POL == POL_FP64>(prm.R, prm.W, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
+    partial_grams<POL == POL_FP64 || POL == POL_SLICED>(prm.R, prm.W, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
     CCG_SYNC_RED(RED_H_S, pk, serial_beta<P>(prm, S));
 
     if (tid == 0) s_int[0] = ldcg(&st->ctrl);
@@ -1683,9 +1843,22 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         double acc = 0.0;
 #pragma unroll 8
         for (int b = 0; b < pk; ++b) acc = fma(ldcg(D + i * p + b), Ts[b * kLd + a], acc);
-        Dn[i * p + a] = ldcg(prm.R + i * p + a) + acc;
+        const double v = ldcg(prm.R + i * p + a) + acc;
+        Dn[i * p + a] = v;
+        if constexpr (kFuseConv) lp_put<LpCfg<POL>::KIND, LpNP<P, POL>::value>(prm, a, i, v);
+      }
+      if constexpr (kFuseConv) {
+        // operand rows of the inactive columns stay zero
+        constexpr int NP = LpNP<P, POL>::value;
+        const int64_t nz = (r1 - r0) * (NP - pk);
+        for (int64_t idx = tid; idx < nz; idx += kThreads) {
+          const int j = pk + (int)(idx / (r1 - r0));
+          lp_put<LpCfg<POL>::KIND, NP>(prm, j, r0 + idx % (r1 - r0), 0.0);
+        }
+        asm volatile("fence.proxy.async.global;" ::: "memory");
       }
       if (!grid_barrier(prm, &ss, &s_err)) return;
+      conv_ready = kFuseConv;
       cur ^= 1;
     }
   }
@@ -1700,7 +1873,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_kernel(const __grid_constant
     solve_body<P, VEC, POL>(prm, reinterpret_cast<double*>(dyn_smem), nullptr);
   } else {
     constexpr int KIND = LpCfg<POL>::KIND;
-    constexpr int NP = LpNP<P>::value;
+    constexpr int NP = LpNP<P, POL>::value;
     using Lay = LpLayout<KIND, NP>;
     using S = tc::Shape<KIND, NP>;
     uint8_t* base = reinterpret_cast<uint8_t*>(
@@ -2020,12 +2193,14 @@ constexpr size_t solver_smem_bytes() {
   if constexpr (POL == POL_FP64) {
     return b;
   } else {
-    return LpLayout<LpCfg<POL>::KIND, LpNP<P>::value>::kBytes + b;
+    return LpLayout<LpCfg<POL>::KIND, LpNP<P, POL>::value>::kBytes + b;
   }
 }
 
 template <int P, bool VEC, int POL>
 void* kernel_ptr() {
+  // dynamic + static shared memory within the 227 KB a CTA may hold
+  static_assert(solver_smem_bytes<P, POL>() + 2048 <= 232448, "shared memory budget");
   return reinterpret_cast<void*>(&fp64_kernel<P, VEC, POL>);
 }
 

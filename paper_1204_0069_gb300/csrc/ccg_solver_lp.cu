@@ -8,6 +8,10 @@
 
 namespace ccg {
 
+// Sliced FP64 policy: ccg_solver_sliced.cu (compiled in parallel).
+void* select_kernel_sliced(int P);
+size_t solver_smem_bytes_sliced(int P);
+
 namespace {
 
 template <int POL>
@@ -42,6 +46,7 @@ void* select_kernel_lp(int P, int pol) {
     case POL_BF16: return select_pol<POL_BF16>(P);
     case POL_FP8: return select_pol<POL_FP8>(P);
     case POL_TF32X3: return select_pol<POL_TF32X3>(P);
+    case POL_SLICED: return select_kernel_sliced(P);
     default: return nullptr;
   }
 }
@@ -50,6 +55,7 @@ size_t solver_smem_bytes_lp(int P, int pol) {
   switch (pol) {
     case POL_BF16: return smem_pol<POL_BF16>(P);
     case POL_FP8: return smem_pol<POL_FP8>(P);
+    case POL_SLICED: return solver_smem_bytes_sliced(P);
     default: return smem_pol<POL_TF32X3>(P);
   }
 }

@@ -15,8 +15,20 @@ namespace tc {
 
 // Kinds of quantised A: BF16; FP8 E4M3 with row scales (operand as two E4M3
 // terms); FP32 multiplied from TF32 halves, (A_hi + A_lo)(D_hi + D_lo) (the
-// low parts split off in shared memory / at conversion).
-enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1, KIND_TF32X3 = 2 };
+// low parts split off in shared memory / at conversion); FP64 split without
+// error into kSlices FP8 slices of small integers (KIND_SLICED, see
+// ccg_lowp.cu): every slice product is exact in the FP32 accumulator.
+enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1, KIND_TF32X3 = 2, KIND_SLICED = 3 };
+
+// Slices of the error-free FP64 split: 4 bits each (integers in [-15, 15],
+// exact in E4M3), 56 bits in all.
+constexpr int kSlices = 14;
+
+__host__ __device__ constexpr int pow2_at_least(int v) {
+  int r = 32;
+  while (r < v) r <<= 1;
+  return r;
+}
 
 constexpr int kBM = 128;          // rows per tile (MMA M)
 constexpr int kRowBytes = 128;    // K bytes per stage = one 128-byte swizzle atom
@@ -25,17 +37,28 @@ constexpr int kTileABytes = kBM * kRowBytes;  // 16 KB
 
 template <int KIND, int NP>
 struct Shape {
-  static constexpr int NB = (KIND == KIND_BF16) ? NP : 2 * NP;   // B rows (hi, lo)
-  static constexpr int kStagesK = (KIND == KIND_TF32X3) ? 4 : kStages;
+  // B rows: NP (BF16), hi and lo (FP8, TF32), kSlices slices per column
+  // (sliced FP64, padded to the MMA's N granularity of 16)
+  static constexpr int NB = (KIND == KIND_BF16)     ? NP
+                            : (KIND == KIND_SLICED) ? (kSlices * NP + 15) / 16 * 16
+                                                    : 2 * NP;
+  // FP32 stages also hold the low halves of A: five fit next to the solver's
+  // serial scratch for N <= 16 operand columns, four for 32; the sliced
+  // operand tile is large for 16 columns
+  static constexpr int kStagesK = (KIND == KIND_TF32X3)   ? ((NP <= 16) ? 5 : 4)
+                                  : (KIND == KIND_SLICED) ? ((NP >= 16) ? 4 : kStages)
+                                                          : kStages;
   static constexpr int kTileBBytes = NB * kRowBytes;
   static constexpr int kTileA2Bytes = (KIND == KIND_TF32X3) ? kTileABytes : 0;  // A_lo
   static constexpr int kStageBytes = kTileABytes + kTileBBytes;  // bytes one TMA stage brings
-  // one MMA covers the operand's hi and lo rows at once (N = NB); the epilogue
-  // adds the two halves of the accumulator
+  // one MMA covers all operand rows (hi and lo, or all slices) at once
+  // (N = NB); the epilogue combines the parts of the accumulator
   static constexpr int NMMA = NB;
-  static constexpr int kTmemCols = (2 * NMMA < 32) ? 32 : 2 * NMMA;  // two accumulators
+  static constexpr int kTmemCols = pow2_at_least(2 * NMMA);  // two accumulators
   static constexpr int kRingBytes = kStagesK * (kTileABytes + kTileA2Bytes + kTileBBytes);
-  static constexpr int kElemBytes = (KIND == KIND_BF16) ? 2 : (KIND == KIND_FP8) ? 1 : 4;
+  static constexpr int kElemBytes = (KIND == KIND_BF16) ? 2 : (KIND == KIND_TF32X3) ? 4 : 1;
+  static_assert(NMMA % 16 == 0 && NMMA <= 256, "MMA N for M = 128");
+  static_assert(kTmemCols <= 512, "tensor memory columns");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
