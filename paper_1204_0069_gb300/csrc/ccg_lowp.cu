@@ -284,11 +284,11 @@ __global__ void quant_fp8_kernel(const double* __restrict__ A, int64_t lda, int6
 // matrix multiplication by using fast routines of matrix multiplication and
 // its applications", Numer. Algorithms 59, 2012, with 4-bit slices).  With e_i
 // the binary exponent of the row's largest |A_ij| (so |A_ij| 2^-e_i < 1),
-// x = A_ij 2^-e_i is written as sum_s q_s 16^-(s+1) + r with integers
-// q_s = trunc(16 x_s) in [-15, 15] (x_0 = x, x_{s+1} = 16 x_s - q_s); every
-// step is exact in FP64 and the remainder |r| < 16^-kSlices is dropped.  The
-// q_s are exact in E4M3, so the tensor cores multiply slices exactly.  Slice
-// s of row i lands in row s * srows + i; scale[i] = 2^e_i.
+// x = A_ij 2^-e_i is written as sign(x) sum_s q_s 16^-(s+1) + r with the hex
+// digits q_s in [0, 15] of |x| (taken from the significand bits, see
+// slice_bits); the remainder |r| < 16^-kSlices is dropped.  sign(x) q_s is
+// exact in E4M3, so the tensor cores multiply slices exactly.  Slice s of row
+// i lands in row s * srows + i; scale[i] = 2^e_i.
 __global__ void slice_fp64_kernel(const double* __restrict__ A, int64_t lda, int64_t n,
                                   uint8_t* __restrict__ Q, int64_t ldq, int64_t srows,
                                   float* __restrict__ scale) {
@@ -309,15 +309,12 @@ __global__ void slice_fp64_kernel(const double* __restrict__ A, int64_t lda, int
   if (red[0] > 0.0) frexp(red[0], &e);
   if (threadIdx.x == 0) scale[i] = ldexpf(1.f, e);
   for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
-    double x = ldexp(A[i * lda + k], -e);
+    uint32_t neg;
+    const uint64_t X = slice_bits(A[i * lda + k], e, &neg);
 #pragma unroll
-    for (int sl = 0; sl < kSlices; ++sl) {
-      x *= 16.0;
-      const double q = trunc(x);
-      x -= q;
+    for (int sl = 0; sl < kSlices; ++sl)
       Q[((int64_t)sl * srows + i) * ldq + k] =
-          (uint8_t)__nv_cvt_double_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
-    }
+          (uint8_t)e4m3_digit((uint32_t)(X >> (52 - 4 * sl)) & 15u, neg);
   }
 }
 

@@ -1264,6 +1264,8 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
           // accumulator column u NP + j holds the exact integer
           // sum_k qA_s(row, k) qV_u(k, j); its weight is 16^-(s+u+2) (s: slice
           // of A of this tile).  Combined in FP64, largest weight first.
+          // weights 16^-(u+2) are compile-time powers of two (one exact FMA per
+          // accumulator); 16^-s is applied once per entry
           const int sl = (int)(t / prm.lp_tiles);
           double out[NP];
 #pragma unroll
@@ -1274,14 +1276,18 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
             tc::tmem_ld<16>(tbase + (uint32_t)(ch * 16), v);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
+              constexpr double kW[tc::kSlices] = {
+                  0x1p-8, 0x1p-12, 0x1p-16, 0x1p-20, 0x1p-24, 0x1p-28, 0x1p-32,
+                  0x1p-36, 0x1p-40, 0x1p-44, 0x1p-48, 0x1p-52, 0x1p-56, 0x1p-60};
               const int col = ch * 16 + q;
               const int u = col / NP;
-              if (u < tc::kSlices) out[col % NP] += ldexp((double)v[q], -4 * (sl + u + 2));
+              if (u < tc::kSlices) out[col % NP] = fma((double)v[q], kW[u], out[col % NP]);
             }
           }
+          const double ws = __longlong_as_double((int64_t)(1023 - 4 * sl) << 52);  // 16^-s
           double* dst = reinterpret_cast<double*>(prm.lp_part) + ((size_t)(c + t) * tc::kBM + row) * NP;
 #pragma unroll
-          for (int j = 0; j < NP; ++j) dst[j] = out[j];
+          for (int j = 0; j < NP; ++j) dst[j] = out[j] * ws;
         } else {
           float v[NM];
           tc::tmem_ld<NM>(tbase, v);
@@ -1362,21 +1368,17 @@ __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, 
     for (int64_t idx = tid; idx < (int64_t)NP * nr; idx += kThreads) {
       const int j = (int)(idx / nr);
       const int64_t i = r0 + (idx - (int64_t)j * nr);
-      double x = 0.0;
+      uint64_t X = 0ull;
+      uint32_t neg = 0u;
       if (j < pk) {
-        const double v = ldcg(V + i * p + j);
         int e;
         frexpf(__ldcg(&st->sigma[j]), &e);  // sigma_j = 2^(e - 1)
-        x = ldexp(v, 1 - e);
+        X = tc::slice_bits(ldcg(V + i * p + j), e - 1, &neg);
       }
 #pragma unroll
-      for (int u = 0; u < tc::kSlices; ++u) {
-        x *= 16.0;
-        const double q = trunc(x);
-        x -= q;
+      for (int u = 0; u < tc::kSlices; ++u)
         o[(int64_t)(u * NP + j) * ldk + i] =
-            (uint8_t)__nv_cvt_double_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
-      }
+            (uint8_t)tc::e4m3_digit((uint32_t)(X >> (52 - 4 * u)) & 15u, neg);
     }
     for (int64_t idx = tid; idx < (int64_t)(Sh::NB - tc::kSlices * NP) * nr; idx += kThreads) {
       const int64_t rrow = tc::kSlices * NP + idx / nr;

@@ -24,6 +24,29 @@ enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1, KIND_TF32X3 = 2, KIND_SLICED = 3 
 // exact in E4M3), 56 bits in all.
 constexpr int kSlices = 14;
 
+// Error-free 4-bit slicing of x = v 2^-e (|v| < 2^e) with integer operations:
+// X = |x| 2^56 truncated to an integer (the bits below 2^-56 are the dropped
+// remainder), digit s = bits 55 - 4s .. 52 - 4s of X, so that
+// x = sign(v) sum_s digit_s 16^-(s+1) + r, |r| < 2^-56.  Each digit is
+// written as FP8 E4M3 of sign(v) digit: for d = 2^k (1 + M/8), k = floor(log2
+// d), the code is (k + 7) << 3 | M (exponent bias 7, three mantissa bits),
+// exact for d <= 15.
+__device__ __forceinline__ uint32_t e4m3_digit(uint32_t d, uint32_t neg) {
+  if (d == 0u) return 0u;
+  const uint32_t k = 31u - (uint32_t)__clz(d);
+  return (((k + 7u) << 3) | ((d << (3u - k)) - 8u)) | (neg << 7);
+}
+__device__ __forceinline__ uint64_t slice_bits(double v, int e, uint32_t* neg) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  *neg = (uint32_t)(b >> 63);
+  const int be = (int)((b >> 52) & 0x7FF);
+  if (be == 0) return 0ull;  // zero or subnormal: below 2^-1022, below any slice here
+  const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // v = m 2^(be - 1075)
+  const int sh = be - 1075 + 56 - e;  // X = m 2^sh
+  if (sh >= 0) return m << sh;        // sh <= 3 since |v| < 2^e
+  return (-sh >= 64) ? 0ull : (m >> (-sh));
+}
+
 __host__ __device__ constexpr int pow2_at_least(int v) {
   int r = 32;
   while (r < v) r <<= 1;
