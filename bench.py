@@ -629,6 +629,7 @@ def main():
                                 "exponential-kernel matrices, n log-uniform [256, 16384], "
                                 "tol {1e-6, 1e-10}, p = 8, 8 workers, budget 150 GB"),
                    "fp64": serving_line(ccg, dev, ccg.FP64),
+                   "fp64_sliced": serving_line(ccg, dev, ccg.FP64_SLICED),
                    "fp32_ir": serving_line(ccg, dev, ccg.FP32_IR)}
 
     cpu = None

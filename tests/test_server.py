@@ -52,7 +52,7 @@ def run_server(ccg, torch, reqs, workers, budget, precision=0, share=16):
     return got, [x.cpu().numpy() for x in xs], st
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32_ir"])
+@pytest.mark.parametrize("precision", [0, 1, 4], ids=["fp64", "fp32_ir", "fp64_sliced"])
 def test_results_alone_equal_results_in_the_mix(env, precision):
     torch, ccg = env["torch"], env["ccg"]
     reqs = requests(torch, 10, seed=5)
