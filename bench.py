@@ -55,7 +55,7 @@ def parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--maxit", type=int, default=0, help="iteration cap (0 = 20 n)")
     ap.add_argument("--profile", default="none",
-                    choices=["none", "solve", "block", "lowp", "mixed", "lowp32"],
+                    choices=["none", "solve", "block", "lowp", "mixed", "lowp32", "sliced"],
                     help="profiling driver: run only K solves, K FP64 block products or K "
                          "tensor-core block products (n = 32768)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision lines")
@@ -168,6 +168,22 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def max_over_ranks(seconds, dist, device):
+    """The largest of the ranks' times (the job's time), or the value itself
+    on a single process."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, seconds):
+    """Whole-job solves/s: every rank solves `steps` systems in `seconds`."""
+    return world * steps / seconds
 
 
 def p_bucket(p):
@@ -498,10 +514,11 @@ def main():
                                   "outer": r.outer_steps, "ms": r.device_ms}), flush=True)
         solver.close()
         return
-    if args.profile == "lowp32":
-        # FP32 (TF32x3) block products of the benchmark matrix through the
-        # persistent kernel's tensor-core A-pass
-        m = solver.lowp_matrix(dA, ccg.LOWP_FP32)
+    if args.profile in ("lowp32", "sliced"):
+        # FP32 (TF32x3) or sliced FP64 block products of the benchmark matrix
+        # through the persistent kernel's tensor-core A-pass
+        m = solver.lowp_matrix(dA, ccg.LOWP_FP32 if args.profile == "lowp32"
+                               else ccg.LOWP_FP64_SLICED)
         V = torch.randn(n, p, dtype=torch.float64, device=dev)
         W = torch.empty(n, p, dtype=torch.float64, device=dev)
         for _ in range(args.warmup + args.steps):
@@ -566,11 +583,8 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     elapsed = e0.elapsed_time(e1) / 1000.0
-    if dist is not None:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = world * args.steps / elapsed
+    elapsed = max_over_ranks(elapsed, dist, dev)
+    value = job_throughput(world, args.steps, elapsed)
     kernel_ms = [r.device_ms for r in results]
     r0 = results[-1]
 
@@ -600,11 +614,8 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         et = f0.elapsed_time(f1) / 1000.0
-        if dist is not None:
-            t = torch.tensor([et], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
-        e2e = {"value": world * args.steps / et, "unit": "solves/s",
+        et = max_over_ranks(et, dist, dev)
+        e2e = {"value": job_throughput(world, args.steps, et), "unit": "solves/s",
                "h2d_bytes_per_step": int(A.nbytes + b.nbytes),
                "d2h_bytes_per_step": int(8 * n + 192)}
 
