@@ -389,12 +389,14 @@ def batched_line(ccg, dev, stream, count=4096, p=4, seed=3):
     for name, prec in (("fp64", ccg.FP64), ("fp32_ir", ccg.FP32_IR)):
         x = torch.zeros_like(bp)
         with ccg.Solver(stream=stream.cuda_stream, precision=prec) as s:
-            s.solve_batched(sizes, Ap, bp, x, p=p, tol=TOL, maxit=20000)   # warm-up
+            s.solve_batched(sizes, Ap, bp, x, p=p, tol=TOL, maxit=20000)   # warm-up, tunes
             summ, st, it, rr = s.solve_batched(sizes, Ap, bp, x, p=p, tol=TOL, maxit=20000)
+            table = s.batch_tuning(p, prec)
         t = summ.device_ms / 1e3
         line = {"solves_per_s": count / t, "ms": summ.device_ms, "status": summ.status_name,
                 "all_ok": bool(np.all(st == 0)), "max_relres": float(np.max(rr)),
-                "iterations_total": int(np.sum(it)), "ctas": summ.ctas}
+                "iterations_total": int(np.sum(it)), "ctas": summ.ctas,
+                "apass_variant_by_size_bucket": table}
         if prec == ccg.FP64:
             flops = float(np.sum(2.0 * np.array(sizes, dtype=np.float64) ** 2 * p * it))
             line["fp64_tflops"] = flops / t / 1e12

@@ -97,6 +97,10 @@ typedef struct {
                                    R_{k+1} = R_k + A D_k alpha_k' (default 0).
                                    Doubles the A traffic.  CCG_FP64 only:
                                    CCG_ERR_INVALID with a mixed precision.   */
+    int batch_autotune;         /* 1 (default): ccg_solve_batched times the
+                                   A-pass variants on each size bucket the
+                                   first time it meets it (see
+                                   ccg_batch_tuning); 0: keep the table       */
 } ccg_config;
 
 typedef struct {
@@ -286,6 +290,25 @@ int ccg_lowp_destroy(ccg_lowp_matrix* m);
 int ccg_solve_batched(ccg_handle* handle, int64_t count, const int64_t* n, const double* A,
                       const double* b, int p, double tol, int maxit, double* x_out,
                       int* status, int* iterations, double* relres, ccg_result* summary);
+
+/*
+ * A-pass variant table of the batched solver (no counterpart in the paper:
+ * an implementation tuning).  Systems fall into size buckets
+ * [2^(k+5), 2^(k+6)), k = 0..7 (the last bucket open-ended); each bucket
+ * uses one shape of the FP64 block product: 0 tiled (a k-chunk of the operand
+ * staged in shared memory for the CTA's rows), 1 per-warp rows with eight
+ * 16-byte loads per lane per step (512 columns), 2 per-warp rows with two
+ * loads per step (128 columns, for short rows).  With cfg.batch_autotune the
+ * first batched call that meets a bucket times the variants on up to two
+ * systems per CTA of that bucket (6 iterations each) and keeps the fastest;
+ * the table lives in the handle, per precision (CCG_FP64 / CCG_FP32_IR) and
+ * agent bucket (p rounded up to a power of two).  Variants 1 and 2 exist for
+ * p <= 8, variant 1 not for p <= 2.
+ *   set = 0: variant[8] receives the table (-1 = not tuned yet).
+ *   set = 1: the table is set from variant[8] (and counts as tuned).
+ * Errors: CCG_ERR_INVALID (bad p or precision, a variant not offered).
+ */
+int ccg_batch_tuning(ccg_handle* handle, int p, int precision, int* variant, int set);
 
 /* ---- Serving: a stream of solve requests --------------------------------- */
 

@@ -24,7 +24,7 @@ EXPORTED = ["ccg_config_init", "ccg_create", "ccg_destroy", "ccg_solve", "ccg_so
             "ccg_version", "ccg_lowp_create", "ccg_lowp_block_product", "ccg_lowp_bytes",
             "ccg_lowp_destroy", "ccg_solve_noalloc", "ccg_solve_mixed", "ccg_solve_batched",
             "ccg_server_config_init", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
-            "ccg_server_stats", "ccg_server_destroy"]
+            "ccg_server_stats", "ccg_server_destroy", "ccg_batch_tuning"]
 FP64, FP32_IR, BF16_IR, FP8_IR, FP64_SLICED = 0, 1, 2, 3, 4
 NOALLOC_MAX_NP = 131072
 LOWP_BF16, LOWP_FP8_E4M3, LOWP_FP32, LOWP_FP64_SLICED = 0, 1, 2, 3
@@ -37,7 +37,7 @@ class Config(ctypes.Structure):
                 ("residual_replacement", ctypes.c_int),
                 ("barrier_timeout_ms", ctypes.c_double), ("max_ctas", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("explicit_residual", ctypes.c_int)]
+                ("explicit_residual", ctypes.c_int), ("batch_autotune", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -116,6 +116,8 @@ def lib():
         L.ccg_solve_batched.argtypes = [_VP, _I64, _VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.POINTER(Result)]
         L.ccg_solve_batched.restype = ctypes.c_int
+        L.ccg_batch_tuning.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int]
+        L.ccg_batch_tuning.restype = ctypes.c_int
         L.ccg_server_config_init.argtypes = [ctypes.POINTER(ServerConfig)]
         L.ccg_server_config_init.restype = None
         L.ccg_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_VP)]
@@ -125,7 +127,7 @@ def lib():
         L.ccg_server_stats.argtypes = [_VP, ctypes.POINTER(ServerStats)]
         L.ccg_server_destroy.argtypes = [_VP]
         for name in ["ccg_server_create", "ccg_server_submit", "ccg_server_poll",
-                     "ccg_server_stats", "ccg_server_destroy"]:
+                     "ccg_server_stats", "ccg_server_destroy", "ccg_batch_tuning"]:
             getattr(L, name).restype = ctypes.c_int
         for name in ["ccg_create", "ccg_destroy", "ccg_solve", "ccg_solve_block",
                      "ccg_block_product", "ccg_selftest_barrier_timeout", "ccg_lowp_create",
@@ -183,7 +185,8 @@ class Solver:
     def __init__(self, device: int = 0, stream=None, rank_tol: float = 1e-12,
                  x0_spread: float = 1.0, seed: int = 0, residual_replacement: bool = True,
                  barrier_timeout_ms: float = 10000.0, max_ctas: int = 0, precision: int = 0,
-                 inner_tol: float = 0.0, max_outer: int = 0, explicit_residual: bool = False):
+                 inner_tol: float = 0.0, max_outer: int = 0, explicit_residual: bool = False,
+                 batch_autotune: bool = True):
         L = lib()
         cfg = Config()
         L.ccg_config_init(ctypes.byref(cfg))
@@ -199,6 +202,7 @@ class Solver:
         cfg.inner_tol = inner_tol
         cfg.max_outer = max_outer
         cfg.explicit_residual = int(bool(explicit_residual))
+        cfg.batch_autotune = int(bool(batch_autotune))
         h = _VP()
         rc = L.ccg_create(ctypes.byref(h), ctypes.byref(cfg))
         if rc != 0:
@@ -281,6 +285,19 @@ class Solver:
                                     int(p), float(tol), int(maxit), _ptr(x_packed),
                                     st.ctypes.data, it.ctypes.data, rr.ctypes.data, ctypes.byref(r))
         return self._res(r), st, it, rr
+
+    def batch_tuning(self, p: int, precision: int = 0, variants=None):
+        """ccg_batch_tuning: returns the A-pass variant table of the batched
+        solver for (p, precision) (-1 = bucket not tuned yet), or sets it."""
+        arr = (ctypes.c_int * 8)()
+        if variants is not None:
+            for k, v in enumerate(variants):
+                arr[k] = int(v)
+        rc = self._lib.ccg_batch_tuning(self._h, int(p), int(precision), arr,
+                                        0 if variants is None else 1)
+        if rc != 0:
+            raise RuntimeError(f"ccg_batch_tuning failed: {STATUS.get(rc, rc)}")
+        return list(arr)
 
     def lowp_matrix(self, A, fmt: int, lda=None) -> "LowpMatrix":
         """Quantised copy of A (ccg_lowp_create) on this handle's device."""

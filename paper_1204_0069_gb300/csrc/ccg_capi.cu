@@ -289,6 +289,7 @@ void ccg_config_init(ccg_config* cfg) {
   cfg->inner_tol = 0.0;
   cfg->max_outer = 0;
   cfg->explicit_residual = 0;
+  cfg->batch_autotune = 1;
 }
 
 int ccg_create(ccg_handle** out, const ccg_config* cfg) {
@@ -302,6 +303,7 @@ int ccg_create(ccg_handle** out, const ccg_config* cfg) {
        c.precision != CCG_FP8_IR && c.precision != CCG_FP64_SLICED) ||
       c.max_ctas < 0 || c.inner_tol < 0.0 || c.max_outer < 0 ||
       (c.explicit_residual != 0 && c.explicit_residual != 1) ||
+      (c.batch_autotune != 0 && c.batch_autotune != 1) ||
       (c.explicit_residual && c.precision != CCG_FP64))
     return CCG_ERR_INVALID;
   int ndev = 0;

@@ -34,6 +34,10 @@ struct ccg_handle_s {
   ccg::DevState* h_state = nullptr;  // pinned host mirror of the device state
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   ccg_lowp_matrix_s* lp = nullptr;  // quantised copy made by ccg_solve (mixed precision)
+  // batched solves: A-pass variant per (FP64 / FP32-IR, agent bucket, size
+  // bucket), and whether the autotuner has settled it
+  int batch_variant[2][6][8] = {};
+  bool batch_known[2][6][8] = {};
   // stream-ordered buffers of a sliced FP64 solve (live during one call)
   void* sliced_dq = nullptr;
   void* sliced_part = nullptr;

@@ -118,6 +118,7 @@ struct Params {
   double rank_tol;
   int replacement;
   int explicit_residual;   // R_{k+1} = A X_{k+1} - b 1^T instead of the recurrence
+  int apass_variant;       // FP64 A-pass shape (0 tiled; 1, 2 narrow with 8 / 2 loads)
   int mode;
   long long timeout_ns;
   unsigned int expected_ctas;  // barrier arrival count
@@ -149,6 +150,7 @@ struct Params {
   double batch_inner_tol;
   int batch_max_outer;
   int* batch_outer;            // refinement steps per system
+  int batch_variant[8];        // A-pass variant per size bucket [2^(b+5), 2^(b+6))
   // FP32 A-pass (POL_F32): A32 row-major with leading dimension a32_ld (a
   // multiple of 4), operand columns as FP32 rows vt32 (stride a32_ld)
   const float* a32;

@@ -293,15 +293,16 @@ __device__ __forceinline__ void load_a_chunk(const double* Arow, int64_t n, int6
   }
 }
 
-// Narrow block product (P <= 2 operand columns, which fit in L1): every warp
-// streams its own rows with 8 independent 16-byte loads in flight per lane and
-// reads the operand through L1; no CTA barrier per k-chunk.  The operand was
-// written before the last grid barrier, whose acquire makes L1 reads fresh.
-template <int P, bool VEC>
+// Narrow block product (few operand columns, which fit in L1): every warp
+// streams its own rows with U independent 16-byte loads in flight per lane
+// (a step covers 64 U columns) and reads the operand through L1; no CTA
+// barrier per k-chunk.  The operand was written before the last grid barrier,
+// whose acquire makes L1 reads fresh.  U = 2 suits short rows (small batched
+// systems), where wider steps would be mostly masked lanes.
+template <int P, bool VEC, int U = 8>
 __device__ void apass_narrow(const Params& prm, const double* __restrict__ V, int ldv,
                              int coff, int pk, double* __restrict__ Y, int ldy,
                              bool sub_b, int64_t r0, int64_t r1) {
-  constexpr int U = 8;                  // double2 loads of A per lane per step
   constexpr int NS = 4;                 // accumulator sets
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -361,13 +362,28 @@ __device__ void apass_narrow(const Params& prm, const double* __restrict__ V, in
 
 // Y[row, c] = sum_k A[row, k] V[k, coff + c] (- b[row]) for the rows
 // [r0, r1) and c < pk.  Vs: shared scratch of 2 * P * VSTR doubles.
-template <int P, bool VEC>
+// VARIANTS (the batched kernels only): prm.apass_variant, chosen per size
+// bucket by the host's autotuner, selects 0 tiled (narrow with 8 loads per
+// step for P <= 2), 1 narrow with 8 loads per step, 2 narrow with 2 loads.
+template <int P, bool VEC, bool VARIANTS = false>
 __device__ void apass(const Params& prm, const double* __restrict__ V, int ldv,
                       int coff, int pk, double* __restrict__ Y, int ldy,
                       bool sub_b, int64_t r0, int64_t r1, double* Vs) {
   if constexpr (P <= 2) {
-    apass_narrow<P, VEC>(prm, V, ldv, coff, pk, Y, ldy, sub_b, r0, r1);
+    if (VARIANTS && prm.apass_variant == 2)
+      apass_narrow<P, VEC, 2>(prm, V, ldv, coff, pk, Y, ldy, sub_b, r0, r1);
+    else
+      apass_narrow<P, VEC, 8>(prm, V, ldv, coff, pk, Y, ldy, sub_b, r0, r1);
     return;
+  } else if constexpr (VARIANTS && P <= 8) {
+    if (prm.apass_variant == 1) {
+      apass_narrow<P, VEC, 8>(prm, V, ldv, coff, pk, Y, ldy, sub_b, r0, r1);
+      return;
+    }
+    if (prm.apass_variant == 2) {
+      apass_narrow<P, VEC, 2>(prm, V, ldv, coff, pk, Y, ldy, sub_b, r0, r1);
+      return;
+    }
   }
   using T = Tile<P>;
   const int lane = threadIdx.x & 31;
@@ -1555,7 +1571,7 @@ __device__ __forceinline__ double splitmix_uniform(unsigned long long seed,
   return (double)(z >> 11) * 0x1.0p-53;
 }
 
-template <int P, bool VEC, int POL>
+template <int P, bool VEC, int POL, bool VARIANTS = false>
 __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCtx* L) {
   __shared__ SyncShared ss;
   __shared__ int s_int[4];
@@ -1605,7 +1621,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
   if constexpr (POL == POL_FP64) {
     if (prm.mode == MODE_BLOCK_PRODUCT) {
       const int q = prm.q;
-      apass<P, VEC>(prm, prm.V, q, 0, q, prm.Wout, q, false, r0, r1, smem);
+      apass<P, VEC, VARIANTS>(prm, prm.V, q, 0, q, prm.Wout, q, false, r0, r1, smem);
       partial_grams<true>(prm.V, prm.Wout, prm.U, prm.U ? prm.V : nullptr, nullptr, q, q, r0, r1,
                     mypart);
       CCG_SYNC_RED(RED_M_G, q, serial_block_product(prm, S));
@@ -1617,7 +1633,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         for (int64_t i = r0 + tid; i < r1; i += kThreads)
           prm.ref_x[i] = fma(prm.ref_coef, prm.ref_delta[i], prm.ref_x[i]);
       if (!grid_barrier(prm, &ss, &s_err)) return;
-      apass<1, VEC>(prm, prm.ref_x, 1, 0, 1, prm.ref_r, 1, true, r0, r1, smem);
+      apass<1, VEC, VARIANTS>(prm, prm.ref_x, 1, 0, 1, prm.ref_r, 1, true, r0, r1, smem);
       partial_sumsq(prm.ref_r, 1, r0, r1, mypart, kSlotScalar);
       __syncthreads();
       partial_sumsq(prm.b, 1, r0, r1, mypart, kSlotVec);
@@ -1671,7 +1687,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
   if (s_int[0] != CTRL_FINISH) {
     // R_0 = A X_0 - b 1^T ; D_0 = R_0
     if constexpr (POL == POL_FP64) {
-      apass<P, VEC>(prm, prm.X, p, 0, p, prm.R, p, true, r0, r1, smem);
+      apass<P, VEC, VARIANTS>(prm, prm.X, p, 0, p, prm.R, p, true, r0, r1, smem);
     } else if constexpr (POL == POL_F32) {
       if (!apass_f32<P>(prm, prm.X, p, prm.R, true, r0, r1, &ss, &s_err)) return;
     } else {
@@ -1726,7 +1742,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       const int jb = ldcg(&st->jbest);
       if constexpr (POL == POL_FP64 || POL == POL_SLICED) {
         // the FP64 true residual always runs on the FP64 pipe
-        apass<1, VEC>(prm, prm.X, p, jb, 1, prm.W, p, true, r0, r1, smem);
+        apass<1, VEC, VARIANTS>(prm, prm.X, p, jb, 1, prm.W, p, true, r0, r1, smem);
         partial_sumsq(prm.W, p, r0, r1, mypart);
         CCG_SYNC_RED(RED_SCALAR, 1, serial_check(prm));
       }
@@ -1735,7 +1751,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
 
     if (ctrl == CTRL_REPLACE) {
       if constexpr (POL == POL_FP64) {
-        apass<P, VEC>(prm, prm.X, p, 0, pk, prm.R, p, true, r0, r1, smem);
+        apass<P, VEC, VARIANTS>(prm, prm.X, p, 0, pk, prm.R, p, true, r0, r1, smem);
       } else if constexpr (POL == POL_SLICED) {
         if (!lp_apass<P, POL>(prm, prm.X, pk, prm.R, true, r0, r1, *L, &ss, &s_err)) return;
       }
@@ -1750,7 +1766,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
 
     // ---- one cCG iteration ----
     if constexpr (POL == POL_FP64) {
-      apass<P, VEC>(prm, D, p, 0, pk, prm.W, p, false, r0, r1, smem);
+      apass<P, VEC, VARIANTS>(prm, D, p, 0, pk, prm.W, p, false, r0, r1, smem);
     } else if constexpr (POL == POL_F32) {
       if (!apass_f32<P>(prm, D, pk, prm.W, false, r0, r1, &ss, &s_err)) return;
     } else {
@@ -1821,7 +1837,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       if constexpr (POL == POL_FP64) {
         if (!rec) {
           if (!grid_barrier(prm, &ss, &s_err)) return;
-          apass<P, VEC>(prm, prm.X, p, 0, pk, prm.R, p, true, r0, r1, smem);
+          apass<P, VEC, VARIANTS>(prm, prm.X, p, 0, pk, prm.R, p, true, r0, r1, smem);
         }
       }
     }
@@ -1958,7 +1974,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_kernel(const __grid_constant
 // register allocation its own.
 template <int P, bool VEC, int POL>
 __device__ __noinline__ void solve_call(const Params& prm, double* smem) {
-  solve_body<P, VEC, POL>(prm, smem, nullptr);
+  solve_body<P, VEC, POL, true>(prm, smem, nullptr);
 }
 
 // Fresh solver state for one system of a batch (thread 0).
@@ -2002,6 +2018,10 @@ __device__ void batch_params(const Params& prm, Params& q, long long i, size_t s
   q.expected_ctas = 1u;
   q.group_ctas = 1;
   q.group_rank = 0;
+  // A-pass variant of the system's size bucket: [2^(b+5), 2^(b+6)), b in 0..7
+  int b = 31 - __clz((unsigned)(d[0] > 0 ? d[0] : 1)) - 5;
+  b = b < 0 ? 0 : (b > 7 ? 7 : b);
+  q.apass_variant = prm.batch_variant[b];
 }
 
 // Batched solver: each CTA takes systems from a queue (largest first) and
@@ -2025,7 +2045,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(const __grid_constan
       __threadfence();
     }
     __syncthreads();
-    solve_body<P, false, POL_FP64>(q, reinterpret_cast<double*>(dyn_smem), nullptr);
+    solve_body<P, false, POL_FP64, true>(q, reinterpret_cast<double*>(dyn_smem), nullptr);
     __syncthreads();
     if (tid == 0) {
       const DevState* st = q.st;

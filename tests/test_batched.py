@@ -116,3 +116,48 @@ def test_batched_rejects_tensor_core_precisions(env):
     with ccg.Solver(precision=ccg.BF16_IR) as s:
         summ, *_ = s.solve_batched([2], z, z, z, p=1, tol=1e-8, maxit=10)
         assert summ.status == -1
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_batched_each_apass_variant_matches_oracle(env, variant):
+    """Every A-pass shape the autotuner may pick gives the FP64 parity bar."""
+    torch, ccg, oracle = env["torch"], env["ccg"], env["oracle"]
+    p = 4
+    sizes = [37, 64, 100, 129, 255, 300, 513, 700]
+    mats, rhs = make_batch(sizes, seed=40 + variant)
+    dA, db, v_off = pack(ccg, torch, sizes, mats, rhs)
+    x = torch.zeros_like(db)
+    with ccg.Solver(batch_autotune=False) as s:
+        s.batch_tuning(p, ccg.FP64, [variant] * 8)
+        summ, st, it, rr = s.solve_batched(sizes, dA, db, x, p=p, tol=1e-10, maxit=10000)
+    assert summ.status == 0, summ
+    xs = x.cpu().numpy()
+    for k, (n, A, b) in enumerate(zip(sizes, mats, rhs)):
+        xi = xs[v_off[k]:v_off[k] + n]
+        X0 = oracle.initial_block(n, p, None, 1.0, 0)
+        ref = oracle.ccg(A, b, X0, 1e-10, 10000)
+        assert np.linalg.norm(b - A @ xi) / np.linalg.norm(b) <= 1.01e-10
+        assert np.linalg.norm(xi - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
+        assert abs(int(it[k]) - ref["iterations"]) <= 2, (k, n, it[k], ref["iterations"])
+
+
+def test_batch_autotuner_fills_the_buckets_it_meets(env):
+    torch, ccg = env["torch"], env["ccg"]
+    p = 4
+    sizes = [40, 50, 90, 200, 210, 600]          # buckets 0, 1, 2, 4
+    mats, rhs = make_batch(sizes, seed=77)
+    dA, db, v_off = pack(ccg, torch, sizes, mats, rhs)
+    x = torch.zeros_like(db)
+    with ccg.Solver() as s:
+        assert s.batch_tuning(p) == [-1] * 8
+        summ, st, it, rr = s.solve_batched(sizes, dA, db, x, p=p, tol=1e-10, maxit=10000)
+        table = s.batch_tuning(p)
+        assert summ.status == 0
+        assert all(table[b] in (0, 1, 2) for b in (0, 1, 2, 4))
+        assert all(table[b] == -1 for b in (3, 5, 6, 7))
+        with pytest.raises(RuntimeError):
+            s.batch_tuning(1, ccg.FP64, [1] * 8)  # no variant 1 for p <= 2
+    xs = x.cpu().numpy()
+    for k, (n, A, b) in enumerate(zip(sizes, mats, rhs)):
+        xi = xs[v_off[k]:v_off[k] + n]
+        assert np.linalg.norm(b - A @ xi) / np.linalg.norm(b) <= 1.01e-10
