@@ -149,3 +149,57 @@ def test_sliced_rejects_more_than_16_agents(env):
     A, b = wl.random_spd(64, seed=1, cond=10.0)
     r, _ = solve_sliced(env, A, b, 17)
     assert r.status == -1
+
+
+# ---- edge cases of the full solve on the sliced product ----
+
+def test_sliced_zero_rhs_and_maxit_zero(env):
+    A, b = wl.random_spd(50, seed=9)
+    r, x = solve_sliced(env, A, np.zeros(50), 4)
+    assert r.status == 0 and r.iterations == 0 and not x.any()
+    torch, ccg = env["torch"], env["ccg"]
+    with ccg.Solver(device=0, precision=ccg.FP64_SLICED) as s:
+        x = torch.zeros(50, dtype=torch.float64, device="cuda")
+        r = s.solve(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), x, p=2, tol=TOL,
+                    maxit=0)
+    assert r.status == 1 and r.iterations == 0
+
+
+def test_sliced_deflation_of_identical_agents(env):
+    torch, ccg = env["torch"], env["ccg"]
+    n = 120
+    A, b = wl.random_spd(n, seed=11, cond=80.0)
+    X0 = np.repeat(wl.random_block(n, 1, seed=12), 5, axis=1)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with ccg.Solver(device=0, precision=ccg.FP64_SLICED) as s:
+        r = s.solve_block(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(),
+                          torch.from_numpy(X0).cuda(), x, tol=TOL, maxit=2000)
+    ref = env["oracle"].ccg(A, b, X0, TOL, 2000)
+    assert r.status == 0 and r.p_final == 1 and r.drops == 4 and ref["p_final"] == 1
+    assert abs(r.iterations - ref["iterations"]) <= 2
+
+
+def test_sliced_nan_and_indefinite(env):
+    A, b = wl.random_spd(30, seed=15)
+    b[4] = np.nan
+    r, _ = solve_sliced(env, A, b, 2)
+    assert r.status == -3
+    n = 40
+    rng = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (Q * np.linspace(-3.0, 5.0, n)) @ Q.T
+    A = 0.5 * (A + A.T)
+    r, _ = solve_sliced(env, A, rng.standard_normal(n), 3)
+    assert r.status == -2
+
+
+@pytest.mark.parametrize("n,p", [(129, 5), (383, 13), (640, 2)])
+def test_sliced_ragged_sizes_and_agent_counts(env, n, p):
+    A, b = wl.random_spd(n, seed=3 * n + p, cond=500.0)
+    r, x = solve_sliced(env, A, b, p)
+    X0 = env["oracle"].initial_block(n, p, None, 1.0, 0)
+    ref = env["oracle"].ccg(A, b, X0, TOL, 20 * n, nthreads=8)
+    assert r.status == 0
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) <= TOL * 1.01
+    assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
+    assert abs(r.iterations - ref["iterations"]) <= 2, (r.iterations, ref["iterations"])
