@@ -626,6 +626,7 @@ __device__ __forceinline__ int red_slot(int set, int q, int e) {
 // The butterfly skips the levels whose partner lanes hold no partial (G <= 16
 // leaves lanes >= G empty; adding their zeros is exact), so lane 0's sum is
 // the same as with all five levels.  The result is valid in lane 0.
+template <bool COMP>
 __device__ __forceinline__ double warp_sum_parts(const Params& prm, int off) {
   const int G = grp_size(prm);
   const int lane = threadIdx.x & 31;
@@ -643,28 +644,38 @@ __device__ __forceinline__ double warp_sum_parts(const Params& prm, int off) {
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-      if (g0 + lane + 32 * k < G) dsum_add(t, h[k], l[k]);
+      if (g0 + lane + 32 * k < G) {
+        if constexpr (COMP) dsum_add(t, h[k], l[k]);
+        else t.hi += h[k] + l[k];
+      }
   }
   int top = 1;
   while (top < G && top < 32) top <<= 1;
   for (int m = top >> 1; m >= 1; m >>= 1) {
     const double oh = __shfl_xor_sync(0xffffffffu, t.hi, m);
-    const double ol = __shfl_xor_sync(0xffffffffu, t.lo, m);
-    const bool low = (threadIdx.x & m) == 0;
-    DSum a = low ? t : DSum{oh, ol};
-    const DSum b = low ? DSum{oh, ol} : t;
-    dsum_add(a, b.hi, b.lo);
-    t = a;
+    if constexpr (COMP) {
+      const double ol = __shfl_xor_sync(0xffffffffu, t.lo, m);
+      const bool low = (threadIdx.x & m) == 0;
+      DSum a = low ? t : DSum{oh, ol};
+      const DSum b = low ? DSum{oh, ol} : t;
+      dsum_add(a, b.hi, b.lo);
+      t = a;
+    } else {
+      t.hi += oh;
+    }
   }
-  return __dadd_rn(t.hi, t.lo);
+  return COMP ? __dadd_rn(t.hi, t.lo) : t.hi;
 }
 
-// Entries w0 + j * wstride (j = 0, 1, ...) of the set, one per warp of this CTA.
+// Entries w0 + j * wstride (j = 0, 1, ...) of the set, one per warp of this
+// CTA.  COMP: compensated (FP64 solves); plain FP64 sums for the inner solves
+// of the mixed-precision paths, whose partials are plain sums already.
+template <bool COMP>
 __device__ void reduce_entries(const Params& prm, int set, int q, int w0, int wstride) {
   const int E = red_count(set, q);
   for (int e = w0 + (int)(threadIdx.x >> 5); e < E; e += wstride) {
     const int off = red_slot(set, q, e);
-    const double v = warp_sum_parts(prm, off);
+    const double v = warp_sum_parts<COMP>(prm, off);
     if ((threadIdx.x & 31) == 0) prm.st->red[off] = v;
   }
 }
@@ -757,7 +768,7 @@ __device__ void stop_test(const Params& prm, SerialSmem& S, int pk, int where) {
 // 3), a pivot below -sqrt(rank_tol) means A is not SPD.  Leaves the factor in
 // S.l, the kept columns in S.keep, their count in S.chol_m and 0 / 2 (not
 // SPD) / 3 (NaN) in S.chol_fail.  Called by warp 0 only.
-template <int NB>
+template <int NB, bool FAST>
 __device__ void warp_chol(const Params& prm, SerialSmem& S, int pk) {
   const int lane = threadIdx.x & 31;
   double r[NB];
@@ -782,9 +793,17 @@ __device__ void warp_chol(const Params& prm, SerialSmem& S, int pk) {
         // iteration count of an ill-conditioned solve follows the rounding of
         // the factor (a reciprocal square root moved it by 9 of 388 at
         // n = 8192, p = 8)
-        const double ljj = sqrt(d);
-        if (lane == j) r[j] = ljj;
-        else if (lane > j) r[j] = r[j] / ljj;
+        if constexpr (FAST) {
+          // inner solves: one reciprocal square root per column (shorter
+          // dependent chain; the refinement does not see the rounding)
+          const double rj = rsqrt(d);
+          if (lane == j) r[j] = d * rj;
+          else if (lane > j) r[j] = r[j] * rj;
+        } else {
+          const double ljj = sqrt(d);
+          if (lane == j) r[j] = ljj;
+          else if (lane > j) r[j] = r[j] / ljj;
+        }
 #pragma unroll
         for (int k = j + 1; k < NB; ++k) {
           const double lkj = __shfl_sync(0xffffffffu, r[j], k);
@@ -805,7 +824,7 @@ __device__ void warp_chol(const Params& prm, SerialSmem& S, int pk) {
 }
 
 // alpha step: M, G -> rank test, factor, alpha_k^T (Algorithm 2 / 3).
-template <int NB>
+template <int NB, bool FAST = false>
 __device__ void serial_alpha(const Params& prm, SerialSmem& S) {
   DevState* st = prm.st;
   const int tid = threadIdx.x;
@@ -835,7 +854,7 @@ __device__ void serial_alpha(const Params& prm, SerialSmem& S) {
   if (tid < pk) {
     const double mjj = S.m[tid * kLd + tid];
     if (mjj < 0.0) S.flag[1] = 1;
-    S.sc[tid] = mjj > 0.0 ? 1.0 / sqrt(mjj) : 0.0;
+    S.sc[tid] = mjj > 0.0 ? (FAST ? rsqrt(mjj) : 1.0 / sqrt(mjj)) : 0.0;
   }
   __syncthreads();
   if (S.flag[0] || S.flag[1]) {
@@ -850,7 +869,7 @@ __device__ void serial_alpha(const Params& prm, SerialSmem& S) {
     else if (c == a) S.l[a * kLd + a] = 1.0;
   }
   __syncthreads();
-  if (tid < 32) warp_chol<NB>(prm, S, pk);
+  if (tid < 32) warp_chol<NB, FAST>(prm, S, pk);
   __syncthreads();
   const int m = S.chol_m;
   if (S.chol_fail) {
@@ -1573,6 +1592,9 @@ __device__ __forceinline__ double splitmix_uniform(unsigned long long seed,
 
 template <int P, bool VEC, int POL, bool VARIANTS = false>
 __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCtx* L) {
+  // FP64 solves keep the oracle's arithmetic in the exchange steps; the inner
+  // solves of the mixed-precision paths take the faster forms
+  constexpr bool kExact = POL == POL_FP64 || POL == POL_SLICED;
   __shared__ SyncShared ss;
   __shared__ int s_int[4];
   __shared__ int s_err;
@@ -1596,14 +1618,14 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     const bool spread_ = G > 1 && red_count(SET, q_) > kRedLocalMax;         \
     if (spread_) {                                                           \
       if (!grid_barrier(prm, &ss, &s_err)) return;                           \
-      reduce_entries(prm, SET, q_, cta * kWarps, G * kWarps);                \
+      reduce_entries<kExact>(prm, SET, q_, cta * kWarps, G * kWarps);                \
     }                                                                        \
     const int f_ = grid_arrive(prm, &ss);                                    \
     if (f_ < 0) return;                                                      \
     if (f_ == 1) {                                                           \
       if (!cta_error(st, &s_err)) {                                          \
         if (!spread_) {                                                      \
-          reduce_entries(prm, SET, q_, 0, kWarps);                           \
+          reduce_entries<kExact>(prm, SET, q_, 0, kWarps);                           \
           __syncthreads();                                                   \
         }                                                                    \
         CALL;                                                                \
@@ -1774,7 +1796,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         return;
     }
     partial_grams<POL == POL_FP64 || POL == POL_SLICED>(D, prm.W, prm.R, D, nullptr, p, pk, r0, r1, mypart);
-    CCG_SYNC_RED(RED_M_G, pk, serial_alpha<P>(prm, S));
+    CCG_SYNC_RED(RED_M_G, pk, (serial_alpha<P, !kExact>(prm, S)));
 
     if (tid == 0) {
       s_int[2] = ldcg(&st->changed);
