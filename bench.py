@@ -232,13 +232,17 @@ def device_exp_kernel(n, seed, length, nugget, dev):
 
 
 def lowp_roofline(ccg, solver, dev, A, p, hbm_gbs, steps=10):
-    """HBM bandwidth of the tensor-core block product (BF16 and FP8 A) on the
-    precision workload (exponential kernel, length 0.1, nugget 1e-3, seed 2)."""
+    """HBM bandwidth of the tensor-core block products (A in BF16, FP8 E4M3,
+    FP32 as TF32 halves, FP64 as 14 exact FP8 slices) on the precision
+    workload (exponential kernel, length 0.1, nugget 1e-3, seed 2).  Bytes are
+    the stored A; the FP32 and sliced products run through the solver's
+    persistent kernel and include its operand conversion, barriers and fixup."""
     import numpy as np
     import torch
     n = A.shape[0]
     out = {}
-    for fmt, name in [(ccg.LOWP_BF16, "bf16"), (ccg.LOWP_FP8_E4M3, "fp8_e4m3")]:
+    for fmt, name in [(ccg.LOWP_BF16, "bf16"), (ccg.LOWP_FP8_E4M3, "fp8_e4m3"),
+                      (ccg.LOWP_FP32, "fp32_tf32_halves"), (ccg.LOWP_FP64_SLICED, "fp64_sliced")]:
         m = solver.lowp_matrix(A, fmt)
         V = torch.randn(n, p, dtype=torch.float64, device=dev)
         W = torch.empty(n, p, dtype=torch.float64, device=dev)
