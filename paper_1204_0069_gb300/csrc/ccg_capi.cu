@@ -204,7 +204,7 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
     const int64_t ldk = ccg::lp::ld_elems(n);
     const int64_t T = (n + 127) / 128;
     const size_t dq_bytes = (size_t)NB * ldk;
-    const size_t part_bytes = (size_t)(G + ccg::lp::kSlicesHost * T) * 128 * NP * sizeof(double);
+    const size_t part_bytes = (size_t)(G + T) * 128 * NP * sizeof(double);
     void* dq = nullptr;
     void* lpart = nullptr;
     e = cudaMallocAsync(&dq, dq_bytes, s);

@@ -60,7 +60,7 @@ int block_product_persistent(ccg_handle* h, const ccg_lowp_matrix_s* m, const do
   int rc = ensure(&h->ws, &h->ws_bytes,
                   Carve::need({(size_t)G * ccg::kPartStride * sizeof(double),
                                sizeof(ccg::DevState), (size_t)NB * ldk * esz,
-                               (size_t)(G + tiles) * 128 * NP * pesz}));
+                               (size_t)(G + T) * 128 * NP * pesz}));
   if (rc != CCG_OK) return rc;
   Carve wc(h->ws);
   ccg::Params prm{};
@@ -69,7 +69,7 @@ int block_product_persistent(ccg_handle* h, const ccg_lowp_matrix_s* m, const do
   prm.part = wc.take<double>((size_t)G * ccg::kPartStride);
   prm.st = wc.take<ccg::DevState>(1);
   prm.lp_dq = wc.take<char>((size_t)NB * ldk * esz);
-  prm.lp_part = reinterpret_cast<float*>(wc.take<char>((size_t)(G + tiles) * 128 * NP * pesz));
+  prm.lp_part = reinterpret_cast<float*>(wc.take<char>((size_t)(G + T) * 128 * NP * pesz));
   prm.mode = ccg::MODE_BLOCK_PRODUCT;
   prm.timeout_ns = (long long)(h->cfg.barrier_timeout_ms * 1e6);
   prm.expected_ctas = (unsigned)G;

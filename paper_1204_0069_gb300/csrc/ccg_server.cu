@@ -78,7 +78,7 @@ double reservation(const ccg_server_config& c, int64_t n, int64_t lda, int p, in
   else if (c.precision == CCG_BF16_IR) lp = (double)n * ld * 2.0 + 32.0 * ld * 2.0;
   else if (c.precision == CCG_FP8_IR) lp = (double)n * ld * 1.0 + 64.0 * ld + 4.0 * n;
   else if (c.precision == CCG_FP64_SLICED)  // 14 slices, operand slices, FP64 partial tiles
-    lp = 14.0 * ld * ld + 4.0 * n + 224.0 * ld + (shares + 14.0 * ld / 128.0) * 128.0 * p * 8.0;
+    lp = 14.0 * ld * ld + 4.0 * n + 224.0 * ld + (shares + ld / 128.0) * 128.0 * p * 8.0;
   const double ws = 5.0 * n * p * 8.0 + shares * ccg::kPartStride * 8.0 + 6.0 * n * 8.0 +
                     (double)(shares + (n + 127) / 128) * 128.0 * 32.0 * 4.0 + 65536.0;
   return a + lp + ws;

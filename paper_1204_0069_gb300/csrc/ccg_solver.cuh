@@ -1063,19 +1063,31 @@ __device__ void serial_block_product(const Params& prm, SerialSmem& S) {
 // max_i |V_ij| (so |V_ij| / sigma_j < 1), from the same per-CTA maxima.
 __device__ void serial_sigma(const Params& prm, int pk, bool pow2 = false) {
   DevState* st = prm.st;
-  if (threadIdx.x < pk) {
-    double m = 0.0;
-    const int G = gridDim.x;
-    for (int g = 0; g < G; ++g)
-      m = fmax(m, ldcg(prm.part + (size_t)g * kPartStride + kSlotVec + threadIdx.x));
+  const int G = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // one warp per column; the per-CTA maxima are non-negative doubles (or
+  // NaN), whose bit patterns order as their values with NaN on top
+  for (int j = warp; j < pk; j += kWarps) {
+    unsigned long long mb = 0ull;
+    for (int g = lane; g < G; g += 32) {
+      const unsigned long long v = (unsigned long long)__double_as_longlong(
+          ldcg(prm.part + (size_t)g * kPartStride + kSlotVec + j));
+      mb = v > mb ? v : mb;
+    }
+    for (int m = 16; m >= 1; m >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, mb, m);
+      mb = o > mb ? o : mb;
+    }
+    if (lane != 0) continue;
+    const double m = __longlong_as_double((long long)mb);
     if (pow2) {
       int e = 0;
       if (m > 0.0) frexp(m, &e);
-      st->sigma[threadIdx.x] = ldexpf(1.f, e);
+      st->sigma[j] = ldexpf(1.f, e);
       if (!(m == m) || isinf(m) || e < -125 || e > 127) set_error(st, ST_ERR_NUMERICAL, 16);
     } else {
       const float mf = (float)m;
-      st->sigma[threadIdx.x] = mf > 0.f ? mf / 448.f : 1.f;
+      st->sigma[j] = mf > 0.f ? mf / 448.f : 1.f;
       if (!(mf == mf) || isinf(mf)) set_error(st, ST_ERR_NUMERICAL, 12);
     }
   }
@@ -1102,9 +1114,10 @@ __device__ void serial_refine(const Params& prm) {
 // The quantised A (BF16, or FP8 E4M3 with row scales) streams through a TMA
 // ring into tcgen05.mma; the operand block is converted to the MMA type by
 // the rows' owners first.  Work is split stream-K over (row tile, k-chunk)
-// units exactly as in the standalone block product; after a grid barrier the
-// owner of each row sums the partial tiles that cover it, in CTA order, and
-// applies the scales.  The ring position, phases and accumulator-buffer
+// units exactly as in the standalone block product (sliced A: over (row tile,
+// slice, k-chunk), so that a CTA sums the slices of a row tile itself); after
+// a grid barrier the owner of each row sums the partial tiles that cover it,
+// in CTA order, and applies the scales.  The ring position, phases and accumulator-buffer
 // counts live in shared memory, so every A-pass resumes where the previous
 // one stopped.
 // --------------------------------------------------------------------------
@@ -1195,10 +1208,16 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
         if (!tc::mbar_wait(tc::smem_u32(&empty[stage]), phase ^ 1u, to, err)) break;
         const int t = (int)(u / kc);
         const int k = (int)(u % kc);
+        // sliced A: tile t = (row tile tr, slice sl) lies in slice plane sl
+        int ty = t;
+        if constexpr (KIND == tc::KIND_SLICED) {
+          const int tr = t / tc::kSlices;
+          ty = (t - tr * tc::kSlices) * (int)prm.lp_tiles + tr;
+        }
         const uint32_t fb = tc::smem_u32(&full[stage]);
         tc::mbar_expect_tx(fb, S::kStageBytes);
         tc::tma_load_2d(tc::smem_u32(sA + stage * tc::kTileABytes), &prm.lp_tmA,
-                        k * prm.lp_kelems, t * tc::kBM, fb);
+                        k * prm.lp_kelems, ty * tc::kBM, fb);
         tc::tma_load_2d(tc::smem_u32(sB + stage * S::kTileBBytes), &prm.lp_tmB,
                         k * prm.lp_kelems, 0, fb);
         L.sh->issued[stage] = (int)phase;
@@ -1287,6 +1306,8 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
     int seg = L.sh->e_seg[quad];
+    // sliced: FP64 sum over the slices of one row tile that this CTA covers
+    double acc[KIND == tc::KIND_SLICED ? NP : 1];
     if (u0 < u1) {
       const int t0 = (int)(u0 / kc);
       const int t1 = (int)((u1 - 1) / kc);
@@ -1300,8 +1321,11 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
           // sum_k qA_s(row, k) qV_u(k, j); its weight is 16^-(s+u+2) (s: slice
           // of A of this tile).  Combined in FP64, largest weight first.
           // weights 16^-(u+2) are compile-time powers of two (one exact FMA per
-          // accumulator); 16^-s is applied once per entry
-          const int sl = (int)(t / prm.lp_tiles);
+          // accumulator); 16^-s is applied once per entry.  Tiles run slice-
+          // minor, so the slices of a row tile are summed here (slice 0 first)
+          // and one partial per (CTA, row tile) is written.
+          const int tr = t / tc::kSlices;
+          const int sl = t - tr * tc::kSlices;
           double out[NP];
 #pragma unroll
           for (int j = 0; j < NP; ++j) out[j] = 0.0;
@@ -1320,9 +1344,14 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
             }
           }
           const double ws = __longlong_as_double((int64_t)(1023 - 4 * sl) << 52);  // 16^-s
-          double* dst = reinterpret_cast<double*>(prm.lp_part) + ((size_t)(c + t) * tc::kBM + row) * NP;
+          const bool open = (t == t0) || (sl == 0);
 #pragma unroll
-          for (int j = 0; j < NP; ++j) dst[j] = out[j] * ws;
+          for (int j = 0; j < NP; ++j) acc[j] = open ? out[j] * ws : fma(out[j], ws, acc[j]);
+          if (t == t1 || sl == tc::kSlices - 1) {
+            double* dst = reinterpret_cast<double*>(prm.lp_part) + ((size_t)(c + tr) * tc::kBM + row) * NP;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) dst[j] = acc[j];
+          }
         } else {
           float v[NM];
           tc::tmem_ld<NM>(tbase, v);
@@ -1382,11 +1411,20 @@ __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, 
   double* mypart = prm.part + (size_t)blockIdx.x * kPartStride;
 
   if constexpr (KIND == tc::KIND_FP8 || KIND == tc::KIND_SLICED) {
-    for (int j = tid; j < pk; j += kThreads) {
-      double m = 0.0;
-      for (int64_t i = r0; i < r1; ++i) m = fmax(m, fabs(ldcg(V + i * p + j)));
-      mypart[kSlotVec + j] = m;
+    // column maxima of |V| over this CTA's rows, as ordered bit patterns
+    // (a NaN stays on top and reaches the check of the column scales)
+    __shared__ unsigned long long s_cmax[P];
+    for (int j = tid; j < pk; j += kThreads) s_cmax[j] = 0ull;
+    __syncthreads();
+    for (int idx = tid; idx < (int)nr * pk; idx += kThreads) {
+      const int li = idx / pk;
+      const int j = idx - li * pk;
+      atomicMax(&s_cmax[j],
+                (unsigned long long)__double_as_longlong(fabs(ldcg(V + (r0 + li) * p + j))));
     }
+    __syncthreads();
+    for (int j = tid; j < pk; j += kThreads)
+      mypart[kSlotVec + j] = __longlong_as_double((long long)s_cmax[j]);
     const int f = grid_arrive(prm, ss);
     if (f < 0) return false;
     if (f == 1) {
@@ -1450,44 +1488,47 @@ __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, 
   const int64_t U = prm.lp_units;
   const int kc = prm.lp_kc;
   if constexpr (KIND == tc::KIND_SLICED) {
-    // FP64 partial tiles, one per (slice of A, row tile) and CTA; the CTA
-    // range of each (slice, row tile) of this CTA's rows is found once
-    __shared__ int s_rng[4][tc::kSlices][2];
-    const int64_t Tp = prm.lp_tiles;
+    // FP64 partial tiles, one per (row tile, CTA) with the slices already
+    // summed; the CTA ranges of the row tiles of this CTA's rows are found
+    // once, kRng row tiles at a time
+    constexpr int kRng = 8;
+    __shared__ int s_rng[kRng][2];
     const int tr0 = (int)(r0 / tc::kBM);
     const int ntr = (nr > 0) ? (int)((r1 - 1) / tc::kBM) - tr0 + 1 : 0;
-    for (int e = tid; e < ntr * tc::kSlices; e += kThreads) {
-      const int q = e / tc::kSlices, sl = e - q * tc::kSlices;
-      const int64_t t = (int64_t)sl * Tp + tr0 + q;
-      const int64_t lo = t * kc, hi = lo + kc;
-      int c0 = (int)((lo * G) / U);
-      while (c0 > 0 && tc::unit_begin(U, G, c0) > lo) --c0;
-      while (tc::unit_begin(U, G, c0 + 1) <= lo) ++c0;
-      int c1 = c0;
-      while (c1 + 1 < G && tc::unit_begin(U, G, c1 + 1) < hi) ++c1;
-      s_rng[q][sl][0] = c0;
-      s_rng[q][sl][1] = c1;
-    }
-    __syncthreads();
     const double* part = reinterpret_cast<const double*>(prm.lp_part);
-    for (int64_t idx = tid; idx < nr * pk; idx += kThreads) {
-      const int64_t i = r0 + idx / pk;
-      const int j = (int)(idx - (idx / pk) * pk);
-      const int tr = (int)(i / tc::kBM);
-      const int rr = (int)(i - (int64_t)tr * tc::kBM);
-      double s = 0.0;
-      for (int sl = 0; sl < tc::kSlices; ++sl) {
-        const int64_t t = (int64_t)sl * Tp + tr;
-        for (int cc = s_rng[tr - tr0][sl][0]; cc <= s_rng[tr - tr0][sl][1]; ++cc) {
-          if (tc::unit_begin(U, G, cc + 1) <= tc::unit_begin(U, G, cc)) continue;
-          s += __ldcg(part + ((size_t)(cc + t) * tc::kBM + rr) * NP + j);
-        }
+    const bool some_empty = U < G;  // with U >= G every CTA holds a unit
+    for (int q0 = 0; q0 < ntr; q0 += kRng) {
+      const int nq = min(kRng, ntr - q0);
+      for (int q = tid; q < nq; q += kThreads) {
+        const int64_t lo = (int64_t)(tr0 + q0 + q) * tc::kSlices * kc;
+        const int64_t hi = lo + (int64_t)tc::kSlices * kc;
+        int c0 = (int)((lo * G) / U);
+        while (c0 > 0 && tc::unit_begin(U, G, c0) > lo) --c0;
+        while (tc::unit_begin(U, G, c0 + 1) <= lo) ++c0;
+        int c1 = c0;
+        while (c1 + 1 < G && tc::unit_begin(U, G, c1 + 1) < hi) ++c1;
+        s_rng[q][0] = c0;
+        s_rng[q][1] = c1;
       }
-      s *= (double)prm.lp_row_scale[i] * (double)__ldcg(&st->sigma[j]);
-      if (sub_b) s -= prm.b[i];
-      Y[i * p + j] = s;
+      __syncthreads();
+      const int64_t ra = max(r0, (int64_t)(tr0 + q0) * tc::kBM);
+      const int64_t rb = min(r1, (int64_t)(tr0 + q0 + nq) * tc::kBM);
+      for (int64_t idx = tid; idx < (rb - ra) * pk; idx += kThreads) {
+        const int64_t i = ra + idx / pk;
+        const int j = (int)(idx - (idx / pk) * pk);
+        const int tr = (int)(i / tc::kBM);
+        const int rr = (int)(i - (int64_t)tr * tc::kBM);
+        double s = 0.0;
+        for (int cc = s_rng[tr - tr0 - q0][0]; cc <= s_rng[tr - tr0 - q0][1]; ++cc) {
+          if (some_empty && tc::unit_begin(U, G, cc + 1) <= tc::unit_begin(U, G, cc)) continue;
+          s += __ldcg(part + ((size_t)(cc + tr) * tc::kBM + rr) * NP + j);
+        }
+        s *= (double)prm.lp_row_scale[i] * (double)__ldcg(&st->sigma[j]);
+        if (sub_b) s -= prm.b[i];
+        Y[i * p + j] = s;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     return true;
   } else {
   for (int64_t idx = tid; idx < nr * pk; idx += kThreads) {
