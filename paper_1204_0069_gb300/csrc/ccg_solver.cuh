@@ -101,6 +101,149 @@ __device__ __forceinline__ void dsum_add(DSum& t, double hi, double lo) {
   t.hi = s;
   t.lo = __dadd_rn(t.lo, __dadd_rn(lo, e));
 }
+// Exact accumulation of products on the integer pipe (a long accumulator in
+// the sense of Kulisch, restricted to a window): sum_i x_i y_i is held as a
+// signed 192-bit integer w times 2^(K - 2203), K the largest biased exponent
+// sum e(x_i) + e(y_i) met so far.  The product of the two 53-bit
+// significands (< 2^106) enters shifted left by 53 - (K - e), so the largest
+// products sit below bit 159 (2^32 terms of headroom) and a product 2^-150
+// below the largest loses its bits beneath the window.  Inf or NaN operands
+// make the result NaN.  The value is returned as an unevaluated pair hi + lo
+// holding the top 106 bits.
+struct XAcc {
+  unsigned long long w0, w1, w2;  // w2 carries the sign (two's complement)
+  int K;
+  int bad;
+};
+__device__ __forceinline__ void xacc_init(XAcc& a) {
+  a.w0 = a.w1 = a.w2 = 0ull;
+  a.K = -4096;
+  a.bad = 0;
+}
+__device__ __forceinline__ void xacc_shr(XAcc& a, int d) {
+  const unsigned long long sg = (unsigned long long)((long long)a.w2 >> 63);
+  if (d >= 192) {
+    a.w0 = a.w1 = a.w2 = sg;
+    return;
+  }
+  while (d >= 64) {
+    a.w0 = a.w1;
+    a.w1 = a.w2;
+    a.w2 = sg;
+    d -= 64;
+  }
+  if (d > 0) {
+    a.w0 = (a.w0 >> d) | (a.w1 << (64 - d));
+    a.w1 = (a.w1 >> d) | (a.w2 << (64 - d));
+    a.w2 = (unsigned long long)((long long)a.w2 >> d);
+  }
+}
+__device__ __forceinline__ void xacc_fma(XAcc& a, double x, double y) {
+  const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long by = (unsigned long long)__double_as_longlong(y);
+  const int ex = (int)(bx >> 52) & 0x7FF, ey = (int)(by >> 52) & 0x7FF;
+  if ((ex == 0x7FF) | (ey == 0x7FF)) a.bad = 1;
+  unsigned long long mx = bx & 0xFFFFFFFFFFFFFull, my = by & 0xFFFFFFFFFFFFFull;
+  if (ex != 0) mx |= 1ull << 52;
+  if (ey != 0) my |= 1ull << 52;
+  if ((mx == 0ull) | (my == 0ull) | a.bad) return;
+  const int e = max(ex, 1) + max(ey, 1);
+  if (e > a.K) {
+    xacc_shr(a, e - a.K);
+    a.K = e;
+  }
+  const int sh = a.K - e;
+  const unsigned long long plo = mx * my, phi = __umul64hi(mx, my);
+  unsigned long long q0, q1, q2 = 0ull;
+  if (sh <= 53) {
+    const int l = 53 - sh;  // 0..53
+    q0 = plo << l;
+    q1 = l ? (phi << l) | (plo >> (64 - l)) : phi;
+    q2 = l ? (phi >> (64 - l)) : 0ull;
+  } else {
+    const int r = sh - 53;
+    if (r >= 128) return;
+    if (r >= 64) {
+      q0 = phi >> (r - 64);
+      q1 = 0ull;
+    } else {
+      q0 = r ? (plo >> r) | (phi << (64 - r)) : plo;
+      q1 = phi >> r;
+    }
+  }
+  if ((bx ^ by) >> 63) {
+    asm("sub.cc.u64 %0, %0, %3;\n\tsubc.cc.u64 %1, %1, %4;\n\tsubc.u64 %2, %2, %5;"
+        : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2) : "l"(q0), "l"(q1), "l"(q2));
+  } else {
+    asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
+        : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2) : "l"(q0), "l"(q1), "l"(q2));
+  }
+}
+// Biased exponent sum of a product (subnormals count as exponent 1): the
+// anchor K of a lane is the largest over its terms.
+__device__ __forceinline__ int xacc_expsum(double x, double y) {
+  const int ex = (int)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF;
+  const int ey = (int)((unsigned long long)__double_as_longlong(y) >> 52) & 0x7FF;
+  return max(ex, 1) + max(ey, 1);
+}
+// As xacc_fma with the anchor fixed beforehand (a.K >= every term's exponent
+// sum): no re-anchoring and no branches, so unrolled terms interleave.  The
+// product P enters as (P 2^53) >> (K - e), shifted by whole words and then
+// bits with selects, and is added or subtracted through its two's complement.
+__device__ __forceinline__ void xacc_fma_k(XAcc& a, double x, double y) {
+  const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long by = (unsigned long long)__double_as_longlong(y);
+  const int ex = (int)(bx >> 52) & 0x7FF, ey = (int)(by >> 52) & 0x7FF;
+  a.bad |= (int)((ex == 0x7FF) | (ey == 0x7FF));
+  const unsigned long long mx = (bx & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(ex != 0) << 52);
+  const unsigned long long my = (by & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(ey != 0) << 52);
+  const int sh = a.K - (max(ex, 1) + max(ey, 1));
+  const unsigned long long plo = mx * my, phi = __umul64hi(mx, my);
+  const unsigned long long q0 = plo << 53, q1 = (phi << 53) | (plo >> 11), q2 = phi >> 11;
+  const int ws = min(sh >> 6, 3), bs = sh & 63;
+  const unsigned long long w0 = ws == 0 ? q0 : ws == 1 ? q1 : ws == 2 ? q2 : 0ull;
+  const unsigned long long w1 = ws == 0 ? q1 : ws == 1 ? q2 : 0ull;
+  const unsigned long long w2 = ws == 0 ? q2 : 0ull;
+  const unsigned long long m = 0ull - ((bx ^ by) >> 63);  // all ones: subtract
+  const unsigned long long r0 = ((w0 >> bs) | ((w1 << 1) << (63 - bs))) ^ m;
+  const unsigned long long r1 = ((w1 >> bs) | ((w2 << 1) << (63 - bs))) ^ m;
+  const unsigned long long r2 = (w2 >> bs) ^ m;
+  asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
+      : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2) : "l"(r0), "l"(r1), "l"(r2));
+  asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, 0;\n\taddc.u64 %2, %2, 0;"
+      : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2) : "l"(m & 1ull));
+}
+// 53 bits of the magnitude m starting at bit pos (zeros below bit 0)
+__device__ __forceinline__ unsigned long long xacc_bits53(const unsigned long long m[3], int pos) {
+  constexpr unsigned long long kMask = (1ull << 53) - 1ull;
+  if (pos <= -53) return 0ull;
+  if (pos < 0) return (m[0] << (-pos)) & kMask;
+  const int limb = pos >> 6, off = pos & 63;
+  const unsigned long long lo = m[limb];
+  const unsigned long long hi = limb < 2 ? m[limb + 1] : 0ull;
+  return (off ? (lo >> off) | (hi << (64 - off)) : lo) & kMask;
+}
+__device__ __forceinline__ DSum xacc_value(const XAcc& a) {
+  if (a.bad) return DSum{__longlong_as_double(0x7FF8000000000000ll), 0.0};
+  const bool neg = (long long)a.w2 < 0;
+  unsigned long long m[3] = {a.w0, a.w1, a.w2};
+  if (neg) {
+    m[0] = ~m[0];
+    m[1] = ~m[1];
+    m[2] = ~m[2];
+    asm("add.cc.u64 %0, %0, 1;\n\taddc.cc.u64 %1, %1, 0;\n\taddc.u64 %2, %2, 0;"
+        : "+l"(m[0]), "+l"(m[1]), "+l"(m[2]));
+  }
+  int b;
+  if (m[2]) b = 191 - __clzll((long long)m[2]);
+  else if (m[1]) b = 127 - __clzll((long long)m[1]);
+  else if (m[0]) b = 63 - __clzll((long long)m[0]);
+  else return DSum{0.0, 0.0};
+  const double hi = ldexp((double)xacc_bits53(m, b - 52), b - 52 + a.K - 2203);
+  const double lo = ldexp((double)xacc_bits53(m, b - 105), b - 105 + a.K - 2203);
+  return neg ? DSum{-hi, -lo} : DSum{hi, lo};
+}
+
 // Warp-wide compensated sum in a fixed butterfly order; all lanes get it.
 __device__ __forceinline__ DSum dsum_warp(DSum t) {
 #pragma unroll
@@ -463,8 +606,9 @@ __device__ void apass(const Params& prm, const double* __restrict__ V, int ldv,
 //                out[kSlotVec + a]    = sum_i S[i,a]^2          (S != NULL)
 // Each entry is summed by a group of T lanes (T = 32 for a few entries, 1
 // when they fill the CTA): lane q of the group takes rows r0 + q, r0 + q + T,
-// ... in order, then the group combines in a fixed butterfly.  COMP: Dot2
-// (hi at [slot], lo at [kPartHalf + slot]); otherwise a plain FP64 sum (lo 0).
+// ... in order, then the group combines in a fixed butterfly.  COMP: each
+// lane's sum exact in a long accumulator, the group's in Dot2 arithmetic (hi
+// at [slot], lo at [kPartHalf + slot]); otherwise a plain FP64 sum (lo 0).
 template <bool COMP>
 __device__ __forceinline__ void grp_combine(DSum& t, int T) {
   for (int m = T >> 1; m >= 1; m >>= 1) {
@@ -485,7 +629,8 @@ __device__ __forceinline__ void grp_combine(DSum& t, int T) {
 template <bool COMP>
 __device__ void partial_grams(const double* U0, const double* V0, const double* U1,
                               const double* V1, const double* S, int ld, int pk,
-                              int64_t r0, int64_t r1, double* out) {
+                              int64_t r0, int64_t r1, double* out, double* stage = nullptr,
+                              int stage_doubles = 0) {
   const int sq = pk * pk;
   const int n0 = U0 ? sq : 0, n1 = U1 ? sq : 0, n2 = S ? pk : 0;
   const int E = n0 + n1 + n2;
@@ -493,6 +638,41 @@ __device__ void partial_grams(const double* U0, const double* V0, const double* 
   while (T < 32 && E * T * 2 <= kThreads) T <<= 1;
   const int groups = kThreads / T;
   const int gi = threadIdx.x / T, q = threadIdx.x % T;
+  // When they fit, the CTA's rows of the operand blocks (first pk columns)
+  // are read once, coalesced, into shared memory (U0 V0 U1 V1 S in order)
+  const int64_t nr = r1 - r0;
+  const int64_t blk = nr * pk;
+  const int nblk = (U0 ? 2 : 0) + (U1 ? 2 : 0) + (S ? 1 : 0);
+  const bool staged = stage != nullptr && nblk * blk <= stage_doubles;
+  const int oU1 = U0 ? 2 * (int)blk : 0;
+  const int oS = oU1 + (U1 ? 2 * (int)blk : 0);
+  if (staged) {
+    // all blocks in one pass, eight loads in flight per thread
+    const int tot = nblk * (int)blk;
+    for (int g0 = threadIdx.x; g0 < tot; g0 += 8 * kThreads) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int g = g0 + u * kThreads;
+        v[u] = 0.0;
+        if (g < tot) {
+          int b = g / (int)blk;
+          const int idx = g - b * (int)blk;
+          const double* B = S;
+          if (U0 && b < 2) B = b == 0 ? U0 : V0;
+          else if (U1 && (b -= U0 ? 2 : 0) < 2) B = b == 0 ? U1 : V1;
+          const int rr = idx / pk;
+          v[u] = ldcg(B + (r0 + rr) * ld + (idx - rr * pk));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int g = g0 + u * kThreads;
+        if (g < tot) stage[g] = v[u];
+      }
+    }
+    __syncthreads();
+  }
   for (int base = 0; base < E; base += groups) {  // same trip count in every warp
     const int e = base + gi;
     const bool act = e < E;
@@ -510,7 +690,28 @@ __device__ void partial_grams(const double* U0, const double* V0, const double* 
       }
     }
     DSum t{0.0, 0.0};
-    if (act) {
+    if (act && staged) {
+      const int ou = e < n0 ? 0 : e < n0 + n1 ? oU1 : oS;
+      const int ov = e < n0 + n1 ? ou + (int)blk : oS;
+      const double* Us = stage + ou + a;
+      const double* Vs = stage + ov + c;
+      XAcc x;
+      xacc_init(x);
+      if constexpr (COMP) {
+        int K = 2;
+        for (int rr = q; rr < (int)nr; rr += T) K = max(K, xacc_expsum(Us[rr * pk], Vs[rr * pk]));
+        x.K = K;
+      }
+#pragma unroll 4
+      for (int rr = q; rr < (int)nr; rr += T) {
+        const double uu = Us[rr * pk], vv = Vs[rr * pk];
+        if constexpr (COMP) xacc_fma_k(x, uu, vv);
+        else t.hi = fma(uu, vv, t.hi);
+      }
+      if constexpr (COMP) t = xacc_value(x);
+    } else if (act) {
+      XAcc x;
+      xacc_init(x);
       int64_t i = r0 + q;
       // blocks of 8 of this lane's rows: 16 independent loads in flight, then
       // the sum in row order
@@ -523,15 +724,16 @@ __device__ void partial_grams(const double* U0, const double* V0, const double* 
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          if constexpr (COMP) dsum_fma(t, u[k], v[k]);
+          if constexpr (COMP) xacc_fma(x, u[k], v[k]);
           else t.hi = fma(u[k], v[k], t.hi);
         }
       }
       for (; i < r1; i += T) {
         const double uu = ldcg(U + i * ld + a), vv = ldcg(Vv + i * ld + c);
-        if constexpr (COMP) dsum_fma(t, uu, vv);
+        if constexpr (COMP) xacc_fma(x, uu, vv);
         else t.hi = fma(uu, vv, t.hi);
       }
+      if constexpr (COMP) t = xacc_value(x);
     }
     grp_combine<COMP>(t, T);
     if (act && q == 0) {
@@ -539,6 +741,7 @@ __device__ void partial_grams(const double* U0, const double* V0, const double* 
       out[kPartHalf + slot] = COMP ? t.lo : 0.0;
     }
   }
+  if (staged) __syncthreads();  // the staging area is shared scratch
 }
 
 // Per-CTA compensated sum of squares of x[i * ld] over the rows [r0, r1)
@@ -576,6 +779,9 @@ struct SerialSmem {
   int chol_m;
   int chol_fail;
 };
+// Every kernel's dynamic shared memory holds a SerialSmem; outside the serial
+// steps the Gram partials use it to stage their operand rows.
+constexpr int kStageDoubles = (int)(sizeof(SerialSmem) / sizeof(double));
 
 // Cross-CTA sums.  A serial step needs the group's sum of some slot entries
 // ("reduction set").  Each entry is summed by one warp: lane l takes the
@@ -1686,7 +1892,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       const int q = prm.q;
       apass<P, VEC, VARIANTS>(prm, prm.V, q, 0, q, prm.Wout, q, false, r0, r1, smem);
       partial_grams<true>(prm.V, prm.Wout, prm.U, prm.U ? prm.V : nullptr, nullptr, q, q, r0, r1,
-                    mypart);
+                    mypart, smem, kStageDoubles);
       CCG_SYNC_RED(RED_M_G, q, serial_block_product(prm, S));
       return;
     }
@@ -1757,7 +1963,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       if (!lp_apass<P, POL>(prm, prm.X, p, prm.R, true, r0, r1, *L, &ss, &s_err)) return;
     }
     for (int64_t idx = r0 * p + tid; idx < r1 * p; idx += kThreads) prm.D0[idx] = ldcg(prm.R + idx);
-    partial_grams<POL == POL_FP64 || POL == POL_SLICED>(nullptr, nullptr, nullptr, nullptr, prm.R, p, p, r0, r1, mypart);
+    partial_grams<POL == POL_FP64 || POL == POL_SLICED>(nullptr, nullptr, nullptr, nullptr, prm.R, p, p, r0, r1, mypart, smem, kStageDoubles);
     CCG_SYNC_RED(RED_S, p, serial_norms(prm, S, false));
   }
 
@@ -1822,7 +2028,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         const int c = (int)(idx % p);
         if (c < pk) D[idx] = ldcg(prm.R + idx);
       }
-      partial_grams<POL == POL_FP64 || POL == POL_SLICED>(nullptr, nullptr, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
+      partial_grams<POL == POL_FP64 || POL == POL_SLICED>(nullptr, nullptr, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart, smem, kStageDoubles);
       CCG_SYNC_RED(RED_S, pk, serial_norms(prm, S, true));
       continue;
     }
@@ -1836,7 +2042,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       if (!lp_apass<P, POL>(prm, D, pk, prm.W, false, r0, r1, *L, &ss, &s_err, conv_ready))
         return;
     }
-    partial_grams<POL == POL_FP64 || POL == POL_SLICED>(D, prm.W, prm.R, D, nullptr, p, pk, r0, r1, mypart);
+    partial_grams<POL == POL_FP64 || POL == POL_SLICED>(D, prm.W, prm.R, D, nullptr, p, pk, r0, r1, mypart, smem, kStageDoubles);
     CCG_SYNC_RED(RED_M_G, pk, (serial_alpha<P, !kExact>(prm, S)));
 
     if (tid == 0) {
@@ -1904,7 +2110,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         }
       }
     }
-    partial_grams<POL == POL_FP64 || POL == POL_SLICED>(prm.R, prm.W, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart);
+    partial_grams<POL == POL_FP64 || POL == POL_SLICED>(prm.R, prm.W, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart, smem, kStageDoubles);
     CCG_SYNC_RED(RED_H_S, pk, serial_beta<P>(prm, S));
 
     if (tid == 0) s_int[0] = ldcg(&st->ctrl);

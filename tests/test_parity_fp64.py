@@ -123,6 +123,50 @@ def test_block_product_and_grams(env, n, q):
     np.testing.assert_allclose(G, U.T @ V, rtol=1e-11, atol=1e-11 * np.abs(U.T @ V).max())
 
 
+def exact_gram(U, V):
+    """U' V in exact rational arithmetic (every double is a dyadic rational)."""
+    from fractions import Fraction
+    Uf = [[Fraction(float(x)) for x in col] for col in U.T]
+    Vf = [[Fraction(float(x)) for x in col] for col in V.T]
+    return [[sum((a * b for a, b in zip(u, v)), Fraction(0)) for v in Vf] for u in Uf]
+
+
+@pytest.mark.parametrize("max_ctas", [0, 1])
+def test_grams_within_one_rounding_of_exact(env, max_ctas):
+    """The Gram sums of Table 1 (M = V'AV, G = U'V) are accumulated exactly
+    per lane in a long integer accumulator and combined across lanes and CTAs
+    in doubled precision, so every entry is the exact sum rounded once, up to
+    2^-90 sum_i |u_i v_i| (plus the FP64 underflow unit).  Inputs: entries
+    over 50 decades, a pair of columns made orthogonal (cancellation to the
+    rounding level), products in the subnormal range and near 1e176."""
+    from fractions import Fraction
+    torch, ccg = env["torch"], env["ccg"]
+    n, q = 3000, 4
+    rng = np.random.default_rng(21)
+    U = rng.standard_normal((n, q)) * np.exp(rng.uniform(-30, 30, (n, q)))
+    V = rng.standard_normal((n, q)) * np.exp(rng.uniform(-30, 30, (n, q)))
+    V[:, 1] -= (U[:, 0] @ V[:, 1]) / (U[:, 0] @ U[:, 0]) * U[:, 0]
+    U[:, 2] *= 1e-160
+    V[:, 2] *= 1e-160
+    U[:, 3] *= 1e150
+    A = np.eye(n)
+    W = torch.zeros((n, q), dtype=torch.float64, device="cuda:0")
+    with ccg.Solver(device=0, max_ctas=max_ctas) as s:
+        rc, M, G, _ = s.block_product(dev(env, A), dev(env, V), W, U=dev(env, U))
+    assert rc == 0
+    assert np.array_equal(W.cpu().numpy(), V)
+    tiny = Fraction(2) ** -1074
+    for got, X, Y in ((G, U, V), (M, V, V)):
+        ex = exact_gram(X, Y)
+        mag = np.abs(X).T @ np.abs(Y)
+        for a in range(q):
+            for c in range(q):
+                S = ex[a][c]
+                err = abs(Fraction(float(got[a, c])) - S)
+                bound = Fraction(2) ** -53 * abs(S) + Fraction(2) ** -90 * Fraction(float(mag[a, c])) * 2 + tiny
+                assert err <= bound, (a, c, float(err), float(bound))
+
+
 def test_block_product_odd_lda_and_host_buffers(env):
     """Unaligned leading dimension (scalar A stream) and host pointers."""
     n, q, lda = 301, 6, 303
