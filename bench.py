@@ -38,7 +38,7 @@ GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a
 # 20-iteration solve of the benchmark system: 22 passes, 11 853.2 MB.  The
 # traffic grows with the passes, so a full solve is scaled from it.
-NCU_BYTES_PER_PASS = {(8192, 8): (11816769792 + 36412928) / 22.0}
+NCU_BYTES_PER_PASS = {(8192, 8): (11814291712 + 45762304) / 22.0}
 
 
 def parse():
