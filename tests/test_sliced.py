@@ -203,3 +203,25 @@ def test_sliced_ragged_sizes_and_agent_counts(env, n, p):
     assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) <= TOL * 1.01
     assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
     assert abs(r.iterations - ref["iterations"]) <= 2, (r.iterations, ref["iterations"])
+
+
+def test_sliced_two_ctas_many_row_tiles_each(env):
+    """Two CTAs own 1050 rows each (9 row tiles of 128): the fixup walks its
+    row tiles in chunks and the Gram partials read the blocks directly (too
+    many rows to stage); the answer is held to the same FP64 bar."""
+    torch, ccg = env["torch"], env["ccg"]
+    n, p = 2100, 4
+    A, b = wl.random_spd(n, seed=23, cond=200.0)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with ccg.Solver(device=0, precision=ccg.FP64_SLICED, max_ctas=2) as s:
+        r = s.solve(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), x, p=p, tol=TOL,
+                    maxit=20 * n)
+    torch.cuda.synchronize()
+    xg = x.cpu().numpy()
+    X0 = env["oracle"].initial_block(n, p, None, 1.0, 0)
+    ref = env["oracle"].ccg(A, b, X0, TOL, 20 * n, nthreads=8)
+    assert r.status == 0 and ref["status"] == 0
+    assert np.linalg.norm(A @ xg - b) / np.linalg.norm(b) <= TOL * 1.01
+    assert np.linalg.norm(xg - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
+    assert abs(r.iterations - ref["iterations"]) <= 2, (r.iterations, ref["iterations"])
+
