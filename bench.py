@@ -10,7 +10,7 @@ agents.  The metric is solves/s.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--p P] [--impl ours|reference]
 
 N > 1 runs independent replicas (one solve per rank per step; the method has
-no cross-GPU data path in this build), launched by torchrun.
+no cross-GPU data path), launched by torchrun.
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead
 (bounded sample of iterations, scaled to a full solve).
 """
@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--maxit", type=int, default=0, help="iteration cap (0 = 20 n)")
     ap.add_argument("--profile", default="none",
                     choices=["none", "solve", "block", "lowp", "mixed", "lowp32", "sliced"],
-                    help="profiling driver: run only K solves, K FP64 block products or K "
+                    help="profiling mode: run only K solves, K FP64 block products or K "
                          "tensor-core block products (n = 32768)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision lines")
     ap.add_argument("--lowp-n", type=int, default=32768,
@@ -549,7 +549,7 @@ def main():
         print(json.dumps({"profile": "lowp", "fmt": args.lowp_fmt, "n": args.lowp_n, "p": p}))
         return
     if args.profile != "none":
-        # profiling driver: the launches ncu captures, nothing else timed
+        # profiling mode: the launches ncu captures, nothing else timed
         V = torch.randn(n, p, dtype=torch.float64, device=dev)
         W = torch.empty(n, p, dtype=torch.float64, device=dev)
         for _ in range(args.warmup + args.steps):

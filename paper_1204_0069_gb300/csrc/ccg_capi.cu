@@ -377,7 +377,7 @@ int ccg_solve(ccg_handle* h, int64_t n, const double* A, int64_t lda, const doub
       if (res) res->status = rc;
       return rc;
     }
-    // (host A is staged again by the mixed driver; a device A is used in place)
+    // (host A is staged again by the mixed-precision host loop; a device A is used in place)
     const int st = ccg_solve_mixed(h, m, n, A, lda, b, x0, p, tol, maxit, x_out, res);
     lowp_destroy_async(h, m);
     return st;
