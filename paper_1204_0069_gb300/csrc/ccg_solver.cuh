@@ -21,9 +21,10 @@
 //
 // The p x p Grams and the norms are inner products that the method treats as
 // exact (Sec. 4 works in exact arithmetic); they decide the matrix stepsizes
-// and the stop test, so they are accumulated with error-free transformations
-// (Dot2 of Ogita, Rump and Oishi 2005: exact products by FMA, TwoSum for the
-// running sum) per CTA and again across CTAs.  Every sum runs in an order
+// and the stop test, so each lane sums its terms exactly in a long integer
+// accumulator (ccg_xacc.h) and the lanes and CTAs are combined with
+// error-free transformations (Dot2 arithmetic of Ogita, Rump and Oishi 2005:
+// TwoSum for the running sum).  Every sum runs in an order
 // fixed by the grid alone, so a solve is bitwise reproducible for a fixed
 // grid.  (The inner solves of the mixed-precision path, whose operator is
 // itself a rounded copy of A, accumulate their Grams in plain FP64.)  On
@@ -42,6 +43,7 @@
 
 #include "ccg_internal.h"
 #include "ccg_tc.cuh"
+#include "ccg_xacc.h"
 
 namespace ccg {
 namespace {
@@ -76,12 +78,9 @@ __device__ void set_error(DevState* st, int code, int where) {
   if (atomicCAS(&st->error, 0, code) == 0) st->err_where = where;
 }
 
-// Compensated accumulation (Dot2).  The intrinsics keep the compiler from
-// contracting the error-free transformations into FMAs.
-struct DSum {
-  double hi;
-  double lo;
-};
+// Compensated accumulation (Dot2) on DSum pairs (ccg_xacc.h).  The
+// intrinsics keep the compiler from contracting the error-free
+// transformations into FMAs.
 __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
   s = __dadd_rn(a, b);
   const double z = __dsub_rn(s, a);
@@ -101,149 +100,6 @@ __device__ __forceinline__ void dsum_add(DSum& t, double hi, double lo) {
   t.hi = s;
   t.lo = __dadd_rn(t.lo, __dadd_rn(lo, e));
 }
-// Exact accumulation of products on the integer pipe (a long accumulator in
-// the sense of Kulisch, restricted to a window): sum_i x_i y_i is held as a
-// signed 192-bit integer w times 2^(K - 2203), K the largest biased exponent
-// sum e(x_i) + e(y_i) met so far.  The product of the two 53-bit
-// significands (< 2^106) enters shifted left by 53 - (K - e), so the largest
-// products sit below bit 159 (2^32 terms of headroom) and a product 2^-150
-// below the largest loses its bits beneath the window.  Inf or NaN operands
-// make the result NaN.  The value is returned as an unevaluated pair hi + lo
-// holding the top 106 bits.
-struct XAcc {
-  unsigned long long w0, w1, w2;  // w2 carries the sign (two's complement)
-  int K;
-  int bad;
-};
-__device__ __forceinline__ void xacc_init(XAcc& a) {
-  a.w0 = a.w1 = a.w2 = 0ull;
-  a.K = -4096;
-  a.bad = 0;
-}
-__device__ __forceinline__ void xacc_shr(XAcc& a, int d) {
-  const unsigned long long sg = (unsigned long long)((long long)a.w2 >> 63);
-  if (d >= 192) {
-    a.w0 = a.w1 = a.w2 = sg;
-    return;
-  }
-  while (d >= 64) {
-    a.w0 = a.w1;
-    a.w1 = a.w2;
-    a.w2 = sg;
-    d -= 64;
-  }
-  if (d > 0) {
-    a.w0 = (a.w0 >> d) | (a.w1 << (64 - d));
-    a.w1 = (a.w1 >> d) | (a.w2 << (64 - d));
-    a.w2 = (unsigned long long)((long long)a.w2 >> d);
-  }
-}
-__device__ __forceinline__ void xacc_fma(XAcc& a, double x, double y) {
-  const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
-  const unsigned long long by = (unsigned long long)__double_as_longlong(y);
-  const int ex = (int)(bx >> 52) & 0x7FF, ey = (int)(by >> 52) & 0x7FF;
-  if ((ex == 0x7FF) | (ey == 0x7FF)) a.bad = 1;
-  unsigned long long mx = bx & 0xFFFFFFFFFFFFFull, my = by & 0xFFFFFFFFFFFFFull;
-  if (ex != 0) mx |= 1ull << 52;
-  if (ey != 0) my |= 1ull << 52;
-  if ((mx == 0ull) | (my == 0ull) | a.bad) return;
-  const int e = max(ex, 1) + max(ey, 1);
-  if (e > a.K) {
-    xacc_shr(a, e - a.K);
-    a.K = e;
-  }
-  const int sh = a.K - e;
-  const unsigned long long plo = mx * my, phi = __umul64hi(mx, my);
-  unsigned long long q0, q1, q2 = 0ull;
-  if (sh <= 53) {
-    const int l = 53 - sh;  // 0..53
-    q0 = plo << l;
-    q1 = l ? (phi << l) | (plo >> (64 - l)) : phi;
-    q2 = l ? (phi >> (64 - l)) : 0ull;
-  } else {
-    const int r = sh - 53;
-    if (r >= 128) return;
-    if (r >= 64) {
-      q0 = phi >> (r - 64);
-      q1 = 0ull;
-    } else {
-      q0 = r ? (plo >> r) | (phi << (64 - r)) : plo;
-      q1 = phi >> r;
-    }
-  }
-  if ((bx ^ by) >> 63) {
-    asm("sub.cc.u64 %0, %0, %3;\n\tsubc.cc.u64 %1, %1, %4;\n\tsubc.u64 %2, %2, %5;"
-        : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2) : "l"(q0), "l"(q1), "l"(q2));
-  } else {
-    asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
-        : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2) : "l"(q0), "l"(q1), "l"(q2));
-  }
-}
-// Biased exponent sum of a product (subnormals count as exponent 1): the
-// anchor K of a lane is the largest over its terms.
-__device__ __forceinline__ int xacc_expsum(double x, double y) {
-  const int ex = (int)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF;
-  const int ey = (int)((unsigned long long)__double_as_longlong(y) >> 52) & 0x7FF;
-  return max(ex, 1) + max(ey, 1);
-}
-// As xacc_fma with the anchor fixed beforehand (a.K >= every term's exponent
-// sum): no re-anchoring and no branches, so unrolled terms interleave.  The
-// product P enters as (P 2^53) >> (K - e), shifted by whole words and then
-// bits with selects, and is added or subtracted through its two's complement.
-__device__ __forceinline__ void xacc_fma_k(XAcc& a, double x, double y) {
-  const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
-  const unsigned long long by = (unsigned long long)__double_as_longlong(y);
-  const int ex = (int)(bx >> 52) & 0x7FF, ey = (int)(by >> 52) & 0x7FF;
-  a.bad |= (int)((ex == 0x7FF) | (ey == 0x7FF));
-  const unsigned long long mx = (bx & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(ex != 0) << 52);
-  const unsigned long long my = (by & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(ey != 0) << 52);
-  const int sh = a.K - (max(ex, 1) + max(ey, 1));
-  const unsigned long long plo = mx * my, phi = __umul64hi(mx, my);
-  const unsigned long long q0 = plo << 53, q1 = (phi << 53) | (plo >> 11), q2 = phi >> 11;
-  const int ws = min(sh >> 6, 3), bs = sh & 63;
-  const unsigned long long w0 = ws == 0 ? q0 : ws == 1 ? q1 : ws == 2 ? q2 : 0ull;
-  const unsigned long long w1 = ws == 0 ? q1 : ws == 1 ? q2 : 0ull;
-  const unsigned long long w2 = ws == 0 ? q2 : 0ull;
-  const unsigned long long m = 0ull - ((bx ^ by) >> 63);  // all ones: subtract
-  const unsigned long long r0 = ((w0 >> bs) | ((w1 << 1) << (63 - bs))) ^ m;
-  const unsigned long long r1 = ((w1 >> bs) | ((w2 << 1) << (63 - bs))) ^ m;
-  const unsigned long long r2 = (w2 >> bs) ^ m;
-  asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
-      : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2) : "l"(r0), "l"(r1), "l"(r2));
-  asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, 0;\n\taddc.u64 %2, %2, 0;"
-      : "+l"(a.w0), "+l"(a.w1), "+l"(a.w2) : "l"(m & 1ull));
-}
-// 53 bits of the magnitude m starting at bit pos (zeros below bit 0)
-__device__ __forceinline__ unsigned long long xacc_bits53(const unsigned long long m[3], int pos) {
-  constexpr unsigned long long kMask = (1ull << 53) - 1ull;
-  if (pos <= -53) return 0ull;
-  if (pos < 0) return (m[0] << (-pos)) & kMask;
-  const int limb = pos >> 6, off = pos & 63;
-  const unsigned long long lo = m[limb];
-  const unsigned long long hi = limb < 2 ? m[limb + 1] : 0ull;
-  return (off ? (lo >> off) | (hi << (64 - off)) : lo) & kMask;
-}
-__device__ __forceinline__ DSum xacc_value(const XAcc& a) {
-  if (a.bad) return DSum{__longlong_as_double(0x7FF8000000000000ll), 0.0};
-  const bool neg = (long long)a.w2 < 0;
-  unsigned long long m[3] = {a.w0, a.w1, a.w2};
-  if (neg) {
-    m[0] = ~m[0];
-    m[1] = ~m[1];
-    m[2] = ~m[2];
-    asm("add.cc.u64 %0, %0, 1;\n\taddc.cc.u64 %1, %1, 0;\n\taddc.u64 %2, %2, 0;"
-        : "+l"(m[0]), "+l"(m[1]), "+l"(m[2]));
-  }
-  int b;
-  if (m[2]) b = 191 - __clzll((long long)m[2]);
-  else if (m[1]) b = 127 - __clzll((long long)m[1]);
-  else if (m[0]) b = 63 - __clzll((long long)m[0]);
-  else return DSum{0.0, 0.0};
-  const double hi = ldexp((double)xacc_bits53(m, b - 52), b - 52 + a.K - 2203);
-  const double lo = ldexp((double)xacc_bits53(m, b - 105), b - 105 + a.K - 2203);
-  return neg ? DSum{-hi, -lo} : DSum{hi, lo};
-}
-
 // Warp-wide compensated sum in a fixed butterfly order; all lanes get it.
 __device__ __forceinline__ DSum dsum_warp(DSum t) {
 #pragma unroll
