@@ -1,5 +1,9 @@
 // ccg_fp64.cu -- instantiations of the persistent solver kernel with the FP64
-// A-pass (ccg_solver.cuh) and the host-side launch helpers for every policy.
+// A-pass and 16-byte loads of A (ccg_solver.cuh), and the host-side launch
+// helpers for every policy.  The other instantiations sit in files of their
+// own so that the library compiles in parallel: ccg_fp64_scalar.cu (FP64
+// A-pass with 8-byte loads), ccg_solver_lp.cu (tensor-core policies),
+// ccg_batch_fp64_kernels.cu and ccg_batch_ir_kernels.cu (batched solver).
 #include <cuda_runtime.h>
 
 #include "ccg_internal.h"
@@ -7,20 +11,23 @@
 
 namespace ccg {
 
-// Tensor-core policies live in ccg_solver_lp.cu (compiled in parallel).
 void* select_kernel_lp(int P, int pol);
 size_t solver_smem_bytes_lp(int P, int pol);
+void* select_kernel_fp64_scalar(int P);
+void* select_batch_fp64(int P);
+void* select_batch_ir(int P);
 
 namespace {
 
 void* select_kernel(int P, bool vec) {
+  if (!vec) return select_kernel_fp64_scalar(P);
   switch (P) {
-    case 1: return vec ? kernel_ptr<1, true, POL_FP64>() : kernel_ptr<1, false, POL_FP64>();
-    case 2: return vec ? kernel_ptr<2, true, POL_FP64>() : kernel_ptr<2, false, POL_FP64>();
-    case 4: return vec ? kernel_ptr<4, true, POL_FP64>() : kernel_ptr<4, false, POL_FP64>();
-    case 8: return vec ? kernel_ptr<8, true, POL_FP64>() : kernel_ptr<8, false, POL_FP64>();
-    case 16: return vec ? kernel_ptr<16, true, POL_FP64>() : kernel_ptr<16, false, POL_FP64>();
-    case 32: return vec ? kernel_ptr<32, true, POL_FP64>() : kernel_ptr<32, false, POL_FP64>();
+    case 1: return kernel_ptr<1, true, POL_FP64>();
+    case 2: return kernel_ptr<2, true, POL_FP64>();
+    case 4: return kernel_ptr<4, true, POL_FP64>();
+    case 8: return kernel_ptr<8, true, POL_FP64>();
+    case 16: return kernel_ptr<16, true, POL_FP64>();
+    case 32: return kernel_ptr<32, true, POL_FP64>();
     default: return nullptr;
   }
 }
@@ -29,23 +36,7 @@ void* select_any(int P, bool vec, int pol) {
   return pol == POL_FP64 ? select_kernel(P, vec) : select_kernel_lp(P, pol);
 }
 
-void* select_batch(int P, bool ir) {
-  switch (P) {
-    case 1: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<1>)
-                      : reinterpret_cast<void*>(&batch_kernel<1>);
-    case 2: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<2>)
-                      : reinterpret_cast<void*>(&batch_kernel<2>);
-    case 4: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<4>)
-                      : reinterpret_cast<void*>(&batch_kernel<4>);
-    case 8: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<8>)
-                      : reinterpret_cast<void*>(&batch_kernel<8>);
-    case 16: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<16>)
-                       : reinterpret_cast<void*>(&batch_kernel<16>);
-    case 32: return ir ? reinterpret_cast<void*>(&batch_ir_kernel<32>)
-                       : reinterpret_cast<void*>(&batch_kernel<32>);
-    default: return nullptr;
-  }
-}
+void* select_batch(int P, bool ir) { return ir ? select_batch_ir(P) : select_batch_fp64(P); }
 
 }  // namespace
 

@@ -1,6 +1,9 @@
 // ccg_solver_lp.cu -- instantiations of the persistent solver kernel whose
-// A-pass runs on the tensor cores (BF16 or FP8 E4M3 A), used by the inner
-// solves of the mixed-precision path.
+// A-pass runs on the tensor cores with A stored in BF16 (policy POL_BF16),
+// and the dispatch over all tensor-core policies.  The other policies sit in
+// files of their own so that the library compiles in parallel:
+// ccg_solver_fp8.cu (FP8 E4M3 with row scales), ccg_solver_tf32.cu (FP32 as
+// TF32 halves), ccg_solver_sliced.cu (FP64 as exact FP8 slices).
 #include <cuda_runtime.h>
 
 #include "ccg_internal.h"
@@ -8,34 +11,35 @@
 
 namespace ccg {
 
-// Sliced FP64 policy: ccg_solver_sliced.cu (compiled in parallel).
+void* select_kernel_fp8(int P);
+size_t solver_smem_bytes_fp8(int P);
+void* select_kernel_tf32(int P);
+size_t solver_smem_bytes_tf32(int P);
 void* select_kernel_sliced(int P);
 size_t solver_smem_bytes_sliced(int P);
 
 namespace {
 
-template <int POL>
-void* select_pol(int P) {
+void* select_bf16(int P) {
   switch (P) {
-    case 1: return kernel_ptr<1, true, POL>();
-    case 2: return kernel_ptr<2, true, POL>();
-    case 4: return kernel_ptr<4, true, POL>();
-    case 8: return kernel_ptr<8, true, POL>();
-    case 16: return kernel_ptr<16, true, POL>();
-    case 32: return kernel_ptr<32, true, POL>();
+    case 1: return kernel_ptr<1, true, POL_BF16>();
+    case 2: return kernel_ptr<2, true, POL_BF16>();
+    case 4: return kernel_ptr<4, true, POL_BF16>();
+    case 8: return kernel_ptr<8, true, POL_BF16>();
+    case 16: return kernel_ptr<16, true, POL_BF16>();
+    case 32: return kernel_ptr<32, true, POL_BF16>();
     default: return nullptr;
   }
 }
 
-template <int POL>
-size_t smem_pol(int P) {
+size_t smem_bf16(int P) {
   switch (P) {
-    case 1: return solver_smem_bytes<1, POL>();
-    case 2: return solver_smem_bytes<2, POL>();
-    case 4: return solver_smem_bytes<4, POL>();
-    case 8: return solver_smem_bytes<8, POL>();
-    case 16: return solver_smem_bytes<16, POL>();
-    default: return solver_smem_bytes<32, POL>();
+    case 1: return solver_smem_bytes<1, POL_BF16>();
+    case 2: return solver_smem_bytes<2, POL_BF16>();
+    case 4: return solver_smem_bytes<4, POL_BF16>();
+    case 8: return solver_smem_bytes<8, POL_BF16>();
+    case 16: return solver_smem_bytes<16, POL_BF16>();
+    default: return solver_smem_bytes<32, POL_BF16>();
   }
 }
 
@@ -43,9 +47,9 @@ size_t smem_pol(int P) {
 
 void* select_kernel_lp(int P, int pol) {
   switch (pol) {
-    case POL_BF16: return select_pol<POL_BF16>(P);
-    case POL_FP8: return select_pol<POL_FP8>(P);
-    case POL_TF32X3: return select_pol<POL_TF32X3>(P);
+    case POL_BF16: return select_bf16(P);
+    case POL_FP8: return select_kernel_fp8(P);
+    case POL_TF32X3: return select_kernel_tf32(P);
     case POL_SLICED: return select_kernel_sliced(P);
     default: return nullptr;
   }
@@ -53,10 +57,10 @@ void* select_kernel_lp(int P, int pol) {
 
 size_t solver_smem_bytes_lp(int P, int pol) {
   switch (pol) {
-    case POL_BF16: return smem_pol<POL_BF16>(P);
-    case POL_FP8: return smem_pol<POL_FP8>(P);
+    case POL_BF16: return smem_bf16(P);
+    case POL_FP8: return solver_smem_bytes_fp8(P);
     case POL_SLICED: return solver_smem_bytes_sliced(P);
-    default: return smem_pol<POL_TF32X3>(P);
+    default: return solver_smem_bytes_tf32(P);
   }
 }
 
