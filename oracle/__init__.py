@@ -15,7 +15,9 @@ LAPACK solve, textbook Hestenes-Stiefel CG at p = 1 (Algorithm 1), the
 properties of Theorem 2 (orthogonality, A-conjugacy, subspace optimality),
 finite termination (Theorem 3), the residual recurrence, the CG error bound of
 Theorem 1, the p = 2 closed forms (Eq. 3 and Eq. 7) and the deflation cases of
-Algorithm 3.  Published SplitMix64 outputs pin the initial-block generator.
+Algorithm 3.  Published SplitMix64 outputs pin the initial-block generator,
+and exact rational sums pin the compensated (Dot2) Gram products
+(tests/test_oracle_gram_exact.py).
 """
 from __future__ import annotations
 
@@ -90,6 +92,8 @@ def _load():
             lib.oracle_true_relres.restype = ctypes.c_double
             lib.oracle_true_relres.argtypes = [ctypes.c_int64, _DP, ctypes.c_int64,
                                                _DP, _DP, ctypes.c_int]
+            lib.oracle_gram.restype = None
+            lib.oracle_gram.argtypes = [ctypes.c_int64, ctypes.c_int, _DP, _DP, _DP]
             lib.oracle_max_threads.restype = ctypes.c_int
             lib.oracle_max_threads.argtypes = []
             _lib = lib
@@ -119,6 +123,18 @@ def initial_block(n: int, p: int, x0=None, spread: float = 1.0, seed: int = 0) -
     _load().oracle_initial_block(n, p, _dp(x0a) if x0a is not None else None,
                                  float(spread), seed & (2**64 - 1), _dp(X0))
     return X0
+
+
+def gram(U, V) -> np.ndarray:
+    """G = U^T V for n x q blocks (q <= 32), each entry a Dot2 sum: the
+    inner products the solver takes for M, G, H and the residue norms."""
+    U = _f64(U); V = _f64(V)
+    if U.ndim != 2 or U.shape != V.shape or not 1 <= U.shape[1] <= 32:
+        raise ValueError("U and V must be n x q with the same shape, q <= 32")
+    n, q = U.shape
+    G = np.empty((q, q), dtype=np.float64)
+    _load().oracle_gram(n, q, _dp(U), _dp(V), _dp(G))
+    return G
 
 
 def true_relres(A, b, x, nthreads: int = 1) -> float:

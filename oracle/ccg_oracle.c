@@ -338,6 +338,14 @@ static double true_relres(int64_t n, const double* A, int64_t lda,
     return sqrt(dot2_value(acc)) / bnorm;
 }
 
+/* The p x p Gram G = U^T V of two n x q row-major blocks (q <= 32), each
+ * entry a Dot2 sum (Ogita, Rump and Oishi 2005) as in every iteration of the
+ * solver below; exported so that the tests can hold it against exact sums. */
+void oracle_gram(int64_t n, int q, const double* U, const double* V, double* G)
+{
+    gram(n, q, U, V, G);
+}
+
 double oracle_true_relres(int64_t n, const double* A, int64_t lda,
                           const double* b, const double* x, int nthreads)
 {
