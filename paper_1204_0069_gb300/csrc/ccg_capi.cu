@@ -1,7 +1,8 @@
 // ccg_capi.cu -- C ABI (include/ccg.h): argument checks, handle and workspace
 // management, host/device buffer staging, and the cooperative launch of the
 // persistent solver kernel.  No compute happens here: every arithmetic step
-// of the solve runs in the kernels of ccg_fp64.cu.
+// of the solve runs in the persistent solver kernels of ccg_solver.cuh
+// (instantiated in ccg_fp64.cu and its sibling files).
 #include <cuda_runtime.h>
 
 #include <algorithm>
