@@ -217,16 +217,24 @@ def solve_bytes(n, p, iters, checks, replacements):
 
 
 def device_exp_kernel(n, seed, length, nugget, dev):
-    """Exponential-kernel SPD matrix built on the device (points drawn with
-    numpy from `seed`); used only for the large tensor-core measurement, whose
-    check is against its own quantised copy."""
+    """Exponential-kernel SPD matrix built on the device, the same family as
+    ``workloads.exp_kernel`` (points drawn with numpy from `seed`); used for
+    the n = 32768 precision workload and the serving pool.  Distances are
+    taken from coordinate differences, sqrt(dx^2 + dy^2 + dz^2), so that the
+    diagonal is exactly 1 + nugget and the matrix exactly symmetric (a
+    distance through |x|^2 + |y|^2 - 2 x.y leaves sqrt(eps) on the diagonal)."""
     import numpy as np
     import torch
     rng = np.random.default_rng(seed)
     z = torch.from_numpy(rng.random((n, 3))).to(dev)
     A = torch.empty((n, n), dtype=torch.float64, device=dev)
     for i0 in range(0, n, 4096):
-        A[i0:i0 + 4096] = torch.exp(-torch.cdist(z[i0:i0 + 4096], z) / length)
+        zi = z[i0:i0 + 4096]
+        d2 = (zi[:, 0:1] - z[:, 0]).square_()
+        for k in (1, 2):
+            d2.add_((zi[:, k:k + 1] - z[:, k]).square_())
+        torch.exp(d2.sqrt_().div_(-length), out=A[i0:i0 + 4096])
+        del d2
     A.diagonal().add_(nugget)
     return A
 

@@ -106,3 +106,21 @@ def test_random_block_shape_and_scale():
     _contig_f64(V)
     assert V.shape == (1000, 4)
     assert 2.7 < V.std() < 3.3
+
+
+@pytest.mark.parametrize("n,length,nugget", [(700, 0.1, 1e-3), (4500, 0.37, 1e-4)])
+def test_device_kernel_builder_matches_the_host_recipe(n, length, nugget):
+    """The on-device builder of the benchmark (run here on the CPU device) gives
+    the exponential-kernel family of the host recipe: same points, diagonal
+    exactly 1 + nugget, exactly symmetric, and every entry within a few ulps
+    of the argument's size (exp multiplies a relative error of its argument
+    t = |z_i - z_j| / length by t); the second case spans a ragged last row
+    chunk."""
+    torch = pytest.importorskip("torch")
+    import bench
+    A = bench.device_exp_kernel(n, 2, length, nugget, torch.device("cpu")).numpy()
+    R, _ = wl.exp_kernel(n, seed=2, length=length, nugget=nugget)
+    np.testing.assert_array_equal(np.diag(A), np.full(n, 1.0 + nugget))
+    np.testing.assert_array_equal(A, A.T)
+    t = -np.log(R - nugget * np.eye(n))
+    assert np.max(np.abs(A - R) / (R * (1.0 + t))) <= 4 * 2.0 ** -52
