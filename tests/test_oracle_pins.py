@@ -358,6 +358,41 @@ def test_affinely_dependent_agent_is_dropped(oracle_mod):
     assert np.array_equal(r3["x"], r2["x"])
 
 
+def test_rank_test_threshold_on_the_scaled_pivot(oracle_mod):
+    """Algorithm 3 drops an agent whose direction is numerically dependent on
+    the agents before it.  Reading of the rank test: Cholesky of the
+    unit-diagonal scaling S M S of M = D'AD, S = diag(M)^(-1/2), in agent
+    order; agent j is dropped when the squared pivot l_jj^2 (the squared
+    A-sine between d_j and the span of the earlier directions) is below
+    rank_tol.  The pivot is computed here with LAPACK, and rank_tol is put a
+    decade on either side of it; the blocks are scaled far from unit norm, so
+    an unscaled pivot, an unsquared one or the wrong agent order changes the
+    decision."""
+    n = 30
+    A, b = wl.random_spd(n, seed=120, cond=20.0)
+    Xab = 50.0 * wl.random_block(n, 2, seed=121)
+    w = wl.random_block(n, 1, seed=122)
+    X0 = np.concatenate([Xab, Xab[:, :1] + 2e-2 * w], axis=1)
+    D0 = A @ X0 - b[:, None]
+    M = D0.T @ A @ D0
+    s = 1.0 / np.sqrt(np.diag(M))
+    L = np.linalg.cholesky(M * s[:, None] * s[None, :])
+    piv = np.diag(L) ** 2
+    assert piv[0] == pytest.approx(1.0) and piv[1] > 1e-2
+    assert 1e-9 < piv[2] < 1e-4          # agent 2 nearly repeats agent 0
+    assert np.diag(M)[2] > 1e3            # far from unit scale
+    kept = oracle_mod.ccg(A, b, X0, tol=1e-14, maxit=1, rank_tol=piv[2] / 10)
+    assert kept["p_final"] == 3 and kept["drops"] == 0
+    dropped = oracle_mod.ccg(A, b, X0, tol=1e-14, maxit=1, rank_tol=piv[2] * 10)
+    assert dropped["p_final"] == 2 and dropped["drops"] == 1
+    assert list(dropped["agents"]) == [0, 1]
+    # the same three starts in another order: the later of the two near
+    # copies is the one dropped
+    Xr = X0[:, [2, 1, 0]]
+    again = oracle_mod.ccg(A, b, Xr, tol=1e-14, maxit=1, rank_tol=piv[2] * 10)
+    assert again["drops"] == 1 and list(again["agents"]) == [0, 1]
+
+
 # --------------------------------------------------------------------------
 # Edge cases and errors
 # --------------------------------------------------------------------------
