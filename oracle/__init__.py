@@ -81,8 +81,11 @@ def _load():
             lib.oracle_ccg.argtypes = [
                 ctypes.c_int64, _DP, ctypes.c_int64, _DP, _DP, ctypes.c_int,
                 ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                ctypes.c_int, ctypes.c_int, _DP, _DP, _IP, ctypes.POINTER(OracleStats),
-                TRACE_FN, ctypes.c_void_p]
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, _DP, _DP, _IP,
+                ctypes.POINTER(OracleStats), TRACE_FN, ctypes.c_void_p]
+            lib.oracle_block_product.restype = None
+            lib.oracle_block_product.argtypes = [ctypes.c_int64, _DP, ctypes.c_int64, _DP,
+                                                 ctypes.c_int, _DP, ctypes.c_int]
             lib.oracle_splitmix64_at.restype = ctypes.c_uint64
             lib.oracle_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             lib.oracle_initial_block.restype = None
@@ -137,6 +140,23 @@ def gram(U, V) -> np.ndarray:
     return G
 
 
+# summation orders of the block product: ascending, descending, blocks of 64,
+# 64 interleaved sums, compensated (Dot2)
+PRODUCT_ORDERS = (0, 1, 2, 3, 4)
+
+
+def block_product(A, V, order: int = 0) -> np.ndarray:
+    """W = A V with each entry a plain FP64 sum in the given order (the block
+    product of the solver, exposed for its pins)."""
+    A = _f64(A); V = _f64(V)
+    n, q = V.shape
+    if A.shape[0] != n or A.shape[1] < n or not 1 <= q <= 32 or order not in PRODUCT_ORDERS:
+        raise ValueError("A must be n x (>= n), V n x q with q <= 32, order in 0..4")
+    W = np.empty((n, q), dtype=np.float64)
+    _load().oracle_block_product(n, _dp(A), A.shape[1], _dp(V), q, _dp(W), int(order))
+    return W
+
+
 def true_relres(A, b, x, nthreads: int = 1) -> float:
     A = _f64(A); b = _f64(b); x = _f64(x)
     n = b.shape[0]
@@ -145,14 +165,18 @@ def true_relres(A, b, x, nthreads: int = 1) -> float:
 
 def ccg(A, b, X0, tol: float, maxit: int, rank_tol: float = 1e-12,
         residual_replacement: bool = True, nthreads: int = 1, trace: bool = False,
-        explicit_residual: bool = False):
+        explicit_residual: bool = False, product_order: int = 0):
     """Run the oracle cCG/mcCG on A x = b from the initial block X0 (n x p).
 
     Returns a dict with x, X (final active block), agents (original indices of
     its columns), status, iterations, agent, p_final, relres_true,
     relres_recur, replacements, drops and, if trace, a list of per-iteration
     states (k, agents, X, R, D, W, alpha, beta) copied out of the callback.
+    product_order picks the summation order of the block product A D (see
+    block_product); 0, ascending, is the default.
     """
+    if product_order not in PRODUCT_ORDERS:
+        raise ValueError("product_order must be one of 0, 1, 2, 3, 4")
     A = _f64(A)
     b = _f64(b)
     X0 = _f64(X0)
@@ -184,7 +208,7 @@ def ccg(A, b, X0, tol: float, maxit: int, rank_tol: float = 1e-12,
     cb = TRACE_FN(_cb) if trace else TRACE_FN()
     rc = _load().oracle_ccg(n, _dp(A), lda, _dp(b), _dp(X0), p, float(tol), int(maxit),
                             float(rank_tol), int(bool(residual_replacement)),
-                            int(bool(explicit_residual)), int(nthreads),
+                            int(bool(explicit_residual)), int(product_order), int(nthreads),
                             _dp(x), _dp(Xf), agents.ctypes.data_as(_IP), ctypes.byref(st),
                             cb, None)
     pf = st.p_final

@@ -55,7 +55,15 @@
  *     Oishi (SIAM J. Sci. Comput. 26, 2005), which is as accurate as a dot
  *     product computed in twice the working precision and then rounded, so
  *     their value does not depend on n or on the order of summation.  The
- *     block product W = A D is a plain sequential sum.
+ *     block product W = A D is a plain FP64 sum of the n products of each
+ *     entry.  The method fixes no summation order; product_order picks one:
+ *     0 = l ascending (the default), 1 = l descending, 2 = blocks of 64
+ *     consecutive terms, each block summed first, 3 = 64 interleaved partial
+ *     sums (term l into sum l mod 64), added in order at the end, 4 = the
+ *     compensated sum Dot2 (nearly the exact sum rounded once).  All five
+ *     are the same definition up to rounding; the tests use them to measure
+ *     how far the iteration count of an ill-conditioned solve moves under
+ *     rounding alone.
  *
  * Storage: every n x p block is row-major with leading dimension p
  * (element (i, j) at [i*p + j]); A is row-major with leading dimension lda.
@@ -131,23 +139,6 @@ void oracle_initial_block(int64_t n, int p, const double* x0, double spread,
 /* Plain dense kernels.                                                      */
 /* ------------------------------------------------------------------------ */
 
-/* W = A V (n x n times n x q).  Each entry is a sequential sum over l. */
-static void mat_block(int64_t n, const double* A, int64_t lda, const double* V,
-                      int q, double* W, int nthreads)
-{
-#pragma omp parallel for schedule(static) num_threads(nthreads)
-    for (int64_t i = 0; i < n; ++i) {
-        double acc[32];
-        for (int c = 0; c < q; ++c) acc[c] = 0.0;
-        const double* Ai = A + i * lda;
-        for (int64_t l = 0; l < n; ++l) {
-            double a = Ai[l];
-            for (int c = 0; c < q; ++c) acc[c] += a * V[l * q + c];
-        }
-        for (int c = 0; c < q; ++c) W[i * q + c] = acc[c];
-    }
-}
-
 /* Error-free transformations, exact in binary64 without FMA contraction:
  * Knuth's TwoSum and Dekker's TwoProduct with Veltkamp's splitting. */
 static void two_sum(double a, double b, double* s, double* e)
@@ -188,6 +179,60 @@ static void dot2_add(dot2_t* t, double x, double y)
 }
 
 static double dot2_value(dot2_t t) { return t.s + t.c; }
+
+/* W = A V (n x n times n x q).  Each entry is the FP64 sum over l of
+ * A_il V_lc, in the order picked by `order` (see the header); order 4 is the
+ * compensated sum Dot2 (as accurate as the plain sum in twice the working
+ * precision, rounded once). */
+#define ORC_BLOCK 64
+static void mat_block(int64_t n, const double* A, int64_t lda, const double* V,
+                      int q, double* W, int nthreads, int order)
+{
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t i = 0; i < n; ++i) {
+        double acc[32];
+        const double* Ai = A + i * lda;
+        for (int c = 0; c < q; ++c) acc[c] = 0.0;
+        if (order == 1) {
+            for (int64_t l = n - 1; l >= 0; --l)
+                for (int c = 0; c < q; ++c) acc[c] += Ai[l] * V[l * q + c];
+        } else if (order == 2) {
+            for (int64_t l0 = 0; l0 < n; l0 += ORC_BLOCK) {
+                double part[32];
+                int64_t l1 = l0 + ORC_BLOCK < n ? l0 + ORC_BLOCK : n;
+                for (int c = 0; c < q; ++c) part[c] = 0.0;
+                for (int64_t l = l0; l < l1; ++l)
+                    for (int c = 0; c < q; ++c) part[c] += Ai[l] * V[l * q + c];
+                for (int c = 0; c < q; ++c) acc[c] += part[c];
+            }
+        } else if (order == 4) {
+            for (int c = 0; c < q; ++c) {
+                dot2_t t = {0.0, 0.0};
+                for (int64_t l = 0; l < n; ++l) dot2_add(&t, Ai[l], V[l * q + c]);
+                acc[c] = dot2_value(t);
+            }
+        } else if (order == 3) {
+            for (int c = 0; c < q; ++c) {
+                double part[ORC_BLOCK];
+                for (int t = 0; t < ORC_BLOCK; ++t) part[t] = 0.0;
+                for (int64_t l = 0; l < n; ++l) part[l % ORC_BLOCK] += Ai[l] * V[l * q + c];
+                for (int t = 0; t < ORC_BLOCK; ++t) acc[c] += part[t];
+            }
+        } else {
+            for (int64_t l = 0; l < n; ++l)
+                for (int c = 0; c < q; ++c) acc[c] += Ai[l] * V[l * q + c];
+        }
+        for (int c = 0; c < q; ++c) W[i * q + c] = acc[c];
+    }
+}
+
+/* W = A V alone, in the given order (for the tests that pin mat_block). */
+void oracle_block_product(int64_t n, const double* A, int64_t lda, const double* V,
+                          int q, double* W, int order)
+{
+    mat_block(n, A, lda, V, q, W, 1, order);
+}
+
 
 /* G = U^T V (q x q), G[a][b] = sum_i U[i][a] V[i][b] (Dot2, i = 0..n-1). */
 static void gram(int64_t n, int q, const double* U, const double* V, double* G)
@@ -362,7 +407,7 @@ double oracle_true_relres(int64_t n, const double* A, int64_t lda,
 int oracle_ccg(int64_t n, const double* A, int64_t lda, const double* b,
                const double* X0, int p, double tol, int maxit,
                double rank_tol, int residual_replacement, int explicit_residual,
-               int nthreads,
+               int product_order, int nthreads,
                double* x_out, double* X_out, int* agents_out,
                oracle_stats* st, oracle_trace_fn cb, void* cb_ctx)
 {
@@ -416,7 +461,7 @@ int oracle_ccg(int64_t n, const double* A, int64_t lda, const double* b,
 
     /* R_0 = A X_0 - b 1^T ; D_0 = R_0   (Algorithm 2, first lines) */
     memcpy(X, X0, sizeof(double) * blk);
-    mat_block(n, A, lda, X, pk, R, nthreads);
+    mat_block(n, A, lda, X, pk, R, nthreads, product_order);
     for (int64_t i = 0; i < n; ++i)
         for (int j = 0; j < pk; ++j) R[i * pk + j] -= b[i];
     memcpy(D, R, sizeof(double) * blk);
@@ -440,7 +485,7 @@ int oracle_ccg(int64_t n, const double* A, int64_t lda, const double* b,
                 break;
             }
             /* residual replacement: R = A X - b 1^T, D = R (restart) */
-            mat_block(n, A, lda, X, pk, R, nthreads);
+            mat_block(n, A, lda, X, pk, R, nthreads, product_order);
             for (int64_t i = 0; i < n; ++i)
                 for (int j = 0; j < pk; ++j) R[i * pk + j] -= b[i];
             memcpy(D, R, sizeof(double) * (size_t)n * pk);
@@ -451,7 +496,7 @@ int oracle_ccg(int64_t n, const double* A, int64_t lda, const double* b,
         }
 
         /* W = A D_k ; M = D^T W (symmetrised) ; G = R^T D   (Table 1) */
-        mat_block(n, A, lda, D, pk, W, nthreads);
+        mat_block(n, A, lda, D, pk, W, nthreads, product_order);
         gram(n, pk, D, W, M);
         for (int a = 0; a < pk; ++a)
             for (int c = 0; c < a; ++c) {
@@ -486,7 +531,7 @@ int oracle_ccg(int64_t n, const double* A, int64_t lda, const double* b,
         add_block_times(n, pk, X, D, alphaT);
         if (explicit_residual) {
             /* Algorithm 2 as printed: R_{k+1} = A X_{k+1} - b 1^T */
-            mat_block(n, A, lda, X, pk, R, nthreads);
+            mat_block(n, A, lda, X, pk, R, nthreads, product_order);
             for (int64_t i = 0; i < n; ++i)
                 for (int j = 0; j < pk; ++j) R[i * pk + j] -= b[i];
         } else {

@@ -25,9 +25,12 @@ enum Kind : int { KIND_BF16 = 0, KIND_FP8 = 1, KIND_TF32X3 = 2, KIND_SLICED = 3 
 constexpr int kSlices = 14;
 
 // Error-free 4-bit slicing of x = v 2^-e (|v| < 2^e) with integer operations:
-// X = |x| 2^56 truncated to an integer (the bits below 2^-56 are the dropped
-// remainder), digit s = bits 55 - 4s .. 52 - 4s of X, so that
-// x = sign(v) sum_s digit_s 16^-(s+1) + r, |r| < 2^-56.  Each digit is
+// X = |x| 2^56 rounded to the nearest integer (halves away from zero; the
+// dropped remainder is at most 2^-57 and has no sign bias, where truncation
+// would shrink every entry toward zero), digit s = bits 55 - 4s .. 52 - 4s
+// of X, so that x = sign(v) sum_s digit_s 16^-(s+1) + r, |r| <= 2^-57.
+// X stays below 2^56: rounding happens only when v has bits below 2^(e-56),
+// i.e. |v| < 2^(e-3).  Each digit is
 // written as FP8 E4M3 of sign(v) digit: for d = 2^k (1 + M/8), k = floor(log2
 // d), the code is (k + 7) << 3 | M (exponent bias 7, three mantissa bits),
 // exact for d <= 15.
@@ -44,7 +47,8 @@ __device__ __forceinline__ uint64_t slice_bits(double v, int e, uint32_t* neg) {
   const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // v = m 2^(be - 1075)
   const int sh = be - 1075 + 56 - e;  // X = m 2^sh
   if (sh >= 0) return m << sh;        // sh <= 3 since |v| < 2^e
-  return (-sh >= 64) ? 0ull : (m >> (-sh));
+  if (-sh > 60) return 0ull;           // |x| 2^56 < 2^-7: rounds to zero
+  return ((m >> (-sh - 1)) + 1ull) >> 1;
 }
 
 __host__ __device__ constexpr int pow2_at_least(int v) {

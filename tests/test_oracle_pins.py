@@ -529,3 +529,102 @@ def test_explicit_and_recurrence_forms_agree_early(oracle_mod):
         assert np.array_equal(s1["agents"], s2["agents"])
         assert np.linalg.norm(s1["X"] - s2["X"]) <= 1e-11 * np.linalg.norm(s1["X"])
     assert abs(r1["iterations"] - r2["iterations"]) <= 2
+
+
+# --------------------------------------------------------------------------
+# Summation order of the block product (a rounding choice the method leaves
+# open).  Each order must be exactly the plain sum it names, and all of them
+# the same solve up to rounding.
+# --------------------------------------------------------------------------
+
+def python_sum(terms, order):
+    """The plain FP64 sum of `terms` in the named order, one Python float
+    addition at a time (Python floats are IEEE binary64)."""
+    n = len(terms)
+    if order == 0:
+        idx = range(n)
+    elif order == 1:
+        idx = range(n - 1, -1, -1)
+    if order in (0, 1):
+        s = 0.0
+        for i in idx:
+            s += terms[i]
+        return s
+    if order == 2:
+        s = 0.0
+        for l0 in range(0, n, 64):
+            part = 0.0
+            for i in range(l0, min(n, l0 + 64)):
+                part += terms[i]
+            s += part
+        return s
+    parts = [0.0] * 64
+    for i in range(n):
+        parts[i % 64] += terms[i]
+    s = 0.0
+    for t in parts:
+        s += t
+    return s
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+def test_block_product_orders_are_the_plain_sums(oracle_mod, order):
+    """Each entry of W = A V equals the sequential Python sum of the products
+    A_il V_lc (each product rounded once) in the order named, bit for bit."""
+    rng = np.random.default_rng(40 + order)
+    n, q = 150, 3
+    A = rng.standard_normal((n, n)) * np.exp(rng.uniform(-8, 8, (n, n)))
+    V = rng.standard_normal((n, q))
+    W = oracle_mod.block_product(A, V, order)
+    for i in range(0, n, 7):
+        for c in range(q):
+            terms = [float(A[i, l] * V[l, c]) for l in range(n)]
+            assert W[i, c] == python_sum(terms, order), (i, c)
+
+
+def test_block_product_orders_within_the_rounding_bound(oracle_mod):
+    """|fl(sum) - sum| <= gamma_n sum |a_l v_l| (Higham, Thm. 3.1) in every
+    order, against the product in extended precision; the orders differ."""
+    rng = np.random.default_rng(44)
+    n, q = 1000, 4
+    A = rng.standard_normal((n, n))
+    V = rng.standard_normal((n, q))
+    exact = (A.astype(np.longdouble) @ V.astype(np.longdouble)).astype(np.float64)
+    u = 2.0 ** -53
+    bound = n * u / (1 - n * u) * (np.abs(A) @ np.abs(V))
+    Ws = [oracle_mod.block_product(A, V, o) for o in oracle_mod.PRODUCT_ORDERS]
+    for W in Ws:
+        assert np.all(np.abs(W - exact) <= bound)
+    assert not np.array_equal(Ws[0], Ws[1])
+
+
+def test_solve_does_not_depend_on_the_product_order_when_well_conditioned(oracle_mod):
+    """On a well-conditioned system (kappa = 9) the five orders give the same
+    iteration count and answers within a few roundings of each other."""
+    A, b = wl.gram_shift(256, seed=0, shift=0.5)
+    X0 = oracle_mod.initial_block(256, 4, None, 1.0, 0)
+    rs = [oracle_mod.ccg(A, b, X0, 1e-10, 2560, product_order=o)
+          for o in oracle_mod.PRODUCT_ORDERS]
+    assert len({r["iterations"] for r in rs}) == 1
+    for r in rs[1:]:
+        assert np.linalg.norm(r["x"] - rs[0]["x"]) <= 1e-13 * np.linalg.norm(rs[0]["x"])
+
+
+def test_compensated_block_product_is_nearly_exact(oracle_mod):
+    """Order 4 (Dot2, Ogita-Rump-Oishi 2005, Prop. 5.5):
+    |W - S| <= u |S| + gamma_n^2 sum_l |A_il V_lc|, S the exact sum (rational
+    arithmetic), on entries with heavy cancellation."""
+    from fractions import Fraction
+    rng = np.random.default_rng(46)
+    n, q = 120, 2
+    A = rng.standard_normal((n, n)) * np.exp(rng.uniform(-20, 20, (n, n)))
+    V = rng.standard_normal((n, q))
+    W = oracle_mod.block_product(A, V, 4)
+    u = 2.0 ** -53
+    g = n * u / (1 - n * u)
+    for i in range(0, n, 11):
+        for c in range(q):
+            S = sum((Fraction(float(A[i, l])) * Fraction(float(V[l, c])) for l in range(n)),
+                    Fraction(0))
+            mag = sum(abs(float(A[i, l]) * float(V[l, c])) for l in range(n))
+            assert abs(Fraction(float(W[i, c])) - S) <= Fraction(u) * abs(S) + Fraction(g * g * mag)

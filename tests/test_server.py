@@ -2,12 +2,21 @@
 
 * every result equals the same request solved alone (same worker share,
   hence the same grid): bitwise, which is within any stated tolerance;
+* every served FP64 result matches the FP64 oracle run on the same request
+  (Algorithm 2 with Algorithm 3's deflation and Algorithm 4's stop rule):
+  iterations within 2 of the oracle's counts over its summation orders
+  (tests/envelope.py; some requests have kappa ~ 5e4) and ||x - x_oracle|| / ||x_oracle|| <= 100 tol (1e-8 at
+  tol 1e-10; two iterates that both stop at relres <= 1e-6 differ at that
+  level); a served
+  mixed-precision result meets its tolerance on the true residual and its
+  distance to the oracle's answer is bounded by the conditioning;
 * requests admitted while others run overlap (peak in-flight > 1);
 * the device-memory budget is never exceeded and a request larger than the
   budget is refused at submission.
 """
 import numpy as np
 import pytest
+from envelope import oracle_counts, within_envelope
 
 from paper_1204_0069_gb300 import workloads as wl
 
@@ -22,7 +31,9 @@ def env():
     from paper_1204_0069_gb300 import build as B
     B.build()
     from paper_1204_0069_gb300 import ccg
-    return dict(torch=torch, ccg=ccg)
+    import oracle
+    oracle.build()
+    return dict(torch=torch, ccg=ccg, oracle=oracle)
 
 
 def requests(torch, count, seed):
@@ -67,6 +78,22 @@ def test_results_alone_equal_results_in_the_mix(env, precision):
                                    precision=precision)
         assert alone[0]["iterations"] == r["iterations"]
         assert np.array_equal(xal[0], xmix[k])
+        # the served answer against the FP64 oracle on the same request
+        n = bn.shape[0]
+        ref, counts, status = oracle_counts(env["oracle"], An, bn,
+                                            env["oracle"].initial_block(n, 8, None, 1.0, 0),
+                                            tol, 50000)
+        assert all(s == 0 for s in status), status
+        err = np.linalg.norm(xmix[k] - ref["x"]) / np.linalg.norm(ref["x"])
+        if precision in (0, 4):
+            # FP64 bar scaled to the request's tolerance: 1e-8 at tol 1e-10
+            assert within_envelope(r["iterations"], counts), (r["iterations"], counts)
+            assert err <= 100.0 * tol, err
+        else:
+            # two answers that both meet relres <= tol differ by at most
+            # 2 kappa tol relative (kappa bounded by ||A||_inf / lambda_min)
+            kappa = np.abs(An).sum(axis=1).max() / (np.min(np.linalg.eigvalsh(An)))
+            assert err <= 2.0 * kappa * tol, (err, kappa)
 
 
 def test_budget_is_respected(env):

@@ -4,12 +4,12 @@ tensor cores from an error-free split of A and D into 4-bit integer slices
 solve built on it.
 
 Block product bound, from the construction: slicing A's row i to 14 slices
-drops less than 2^-56 of 2^e_i <= 2 max_k |A_ik| per entry (same for D's
-column j), every slice product is exact in the FP32 accumulator, and the
+(rounded to nearest) drops at most 2^-57 of 2^e_i <= 2 max_k |A_ik| per entry
+(same for D's column j), every slice product is exact in the FP32 accumulator, and the
 slices are combined in FP64 (at most ~60 roundings of partial sums bounded by
 (|A| |D|)_ij).  So
 
-  |W - A D|_ij <= 2^-55 (max_k |A_ik| sum_k |D_kj| + max_k |D_kj| sum_k |A_ik|)
+  |W - A D|_ij <= 2^-56 (max_k |A_ik| sum_k |D_kj| + max_k |D_kj| sum_k |A_ik|)
                  + 64 * 2^-53 (|A| |D|)_ij,
 
 checked against the product in extended precision (numpy longdouble).  The
@@ -60,7 +60,7 @@ def test_sliced_block_product_is_fp64_accurate(env, n, q):
     Wg = W.cpu().numpy()
     ref = exact_product(A, V)
     absA, absV = np.abs(A), np.abs(V)
-    bound = (2.0 ** -55 * (absA.max(axis=1)[:, None] * absV.sum(axis=0)[None, :]
+    bound = (2.0 ** -56 * (absA.max(axis=1)[:, None] * absV.sum(axis=0)[None, :]
                            + absV.max(axis=0)[None, :] * absA.sum(axis=1)[:, None])
              + 64 * 2.0 ** -53 * (absA @ absV))
     err = np.abs(Wg - ref)
