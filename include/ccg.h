@@ -67,9 +67,9 @@ typedef enum {
                                 slices of 4-bit integers each (the splitting of
                                 Ozaki, Ogita, Oishi and Rump, Numer. Algorithms
                                 59, 2012): every slice product is exact, the
-                                slices are combined in FP64, and the truncation
-                                error is below 2^-56 of each row's and column's
-                                largest entry.  The sliced copy of A (14 bytes per
+                                slices are combined in FP64, and the slicing
+                                (rounded to nearest) drops at most 2^-57 of each
+                                row's and column's largest power of two.  The sliced copy of A (14 bytes per
                                 entry) is made in each call; p <= 16.  Rows of A
                                 and columns of D_k must have their largest
                                 magnitude in [2^-125, 2^127]                   */
@@ -101,7 +101,34 @@ typedef struct {
                                    A-pass variants on each size bucket the
                                    first time it meets it (see
                                    ccg_batch_tuning); 0: keep the table       */
+    int mixed_method;           /* mixed precision: CCG_MIXED_AUTO (default:
+                                   preconditioned FP64 cCG for BF16 and FP8,
+                                   refinement for FP32), CCG_MIXED_REFINE or
+                                   CCG_MIXED_PRECOND                          */
+    int cheb_degree;            /* CCG_MIXED_PRECOND: products with the
+                                   quantised A per preconditioner application;
+                                   0 = 32                                     */
+    double cheb_ratio;          /* CCG_MIXED_PRECOND: lower end of the
+                                   Chebyshev interval as a fraction of the
+                                   upper end (a bound on the largest
+                                   eigenvalue); 0 = 3e-4                      */
 } ccg_config;
+
+/* Mixed-precision methods (ccg_config.mixed_method).
+ *   CCG_MIXED_REFINE : FP64 iterative refinement x += d around inner cCG solves
+ *                      on the quantised A (needs kappa(A) u_q < 1 to contract).
+ *   CCG_MIXED_PRECOND: FP64 cCG (Algorithm 2, every product with the FP64 A,
+ *                      formed exactly from FP8 slices for p <= 16) whose new
+ *                      directions come from preconditioned residues:
+ *                      D_{k+1} = Z_{k+1} + D_k beta_k', Z = q(A_q) R with q a
+ *                      Chebyshev polynomial in the quantised A (cheb_degree
+ *                      tensor-core products, no inner products), and
+ *                      beta_k' = -(D_k'AD_k)^{-1} (AD_k)' Z_{k+1}, which keeps
+ *                      D_{k+1} A-orthogonal to D_k however the preconditioner
+ *                      varies (the flexible form).  Converges to the FP64
+ *                      tolerance whatever kappa(A) u_q, since the quantised A
+ *                      only shapes the directions.                            */
+enum { CCG_MIXED_AUTO = 0, CCG_MIXED_REFINE = 1, CCG_MIXED_PRECOND = 2 };
 
 typedef struct {
     int status;           /* ccg_status of the solve                          */
@@ -114,7 +141,9 @@ typedef struct {
     double relres_recur;  /* min_j ||R e_j|| / ||b|| from the recurrence      */
     float device_ms;      /* device time of the solve kernel(s)               */
     int ctas;             /* CTAs of the persistent launch                    */
-    int outer_steps;      /* mixed precision: refinement steps taken          */
+    int outer_steps;      /* mixed precision: refinement steps taken, or (with
+                             CCG_MIXED_PRECOND) preconditioner applications;
+                             iterations then counts the FP64 iterations      */
 } ccg_result;
 
 /* Fill *cfg with the defaults listed above. */
@@ -228,18 +257,32 @@ int ccg_lowp_block_product(ccg_handle* handle, const ccg_lowp_matrix* m, const d
                            double* W, float* device_ms);
 
 /*
- * Mixed-precision solve of A x = b (FP64 result): iterative refinement in
- * FP64 around inner cCG solves whose block products use the quantised copy
- * `lpA` of A on the tensor cores.  Each step computes the FP64 residual
- * r = b - A x, solves A_lp d = r with p agents to the relative tolerance
- * cfg.inner_tol (the recurrence residual decides), and updates x += d.  The
- * solve stops when ||b - A x|| / ||b|| <= tol (CCG_OK), or returns the best x
- * with CCG_NOT_CONVERGED when maxit inner iterations or cfg.max_outer steps
- * are used up, two steps in a row fail to improve the residual, or an inner
- * solve breaks down (A_lp not positive definite) -- refinement contracts only
- * when A_lp approximates A well enough for the system's conditioning.  x0 may be NULL (zeros).  res->iterations counts inner
- * iterations, res->outer_steps refinement steps, res->relres_true is the FP64
- * relative residual of x_out.  lpA must have been made from this A.
+ * Mixed-precision solve of A x = b (FP64 result) with the quantised copy `lpA`
+ * of A on the tensor cores, by cfg.mixed_method:
+ *
+ * CCG_MIXED_REFINE (auto for FP32): iterative refinement in FP64 around inner
+ * cCG solves on lpA.  Each step computes the FP64 residual r = b - A x, solves
+ * A_lp d = r with p agents to the relative tolerance cfg.inner_tol (the
+ * recurrence residual decides), and updates x += d.  The solve stops when
+ * ||b - A x|| / ||b|| <= tol (CCG_OK), or returns the best x with
+ * CCG_NOT_CONVERGED when maxit inner iterations or cfg.max_outer steps are
+ * used up, two steps in a row fail to improve the residual, or an inner solve
+ * breaks down (A_lp not positive definite) -- refinement contracts only when
+ * A_lp approximates A well enough for the system's conditioning.
+ * res->iterations counts inner iterations, res->outer_steps refinement steps.
+ *
+ * CCG_MIXED_PRECOND (auto for BF16 and FP8): FP64 cCG on A (Algorithm 2 with
+ * Algorithm 3's deflation and Algorithm 4's stop rule and residual check) in
+ * which each new direction block is built from Z_{k+1} = q(A_lp) R_{k+1}, a
+ * Chebyshev polynomial of cfg.cheb_degree products with A_lp on the interval
+ * [cfg.cheb_ratio h, h], h a bound on the largest eigenvalue of A_lp (its
+ * largest absolute row sum).  The block products of the FP64 iteration are
+ * formed exactly from FP8 slices of A (as CCG_FP64_SLICED) for p <= 16, on the
+ * FP64 pipe above.  res->iterations counts FP64 iterations, res->outer_steps
+ * preconditioner applications.
+ *
+ * x0 may be NULL (zeros).  res->relres_true is the FP64 relative residual of
+ * x_out.  lpA must have been made from this A.
  */
 int ccg_solve_mixed(ccg_handle* handle, const ccg_lowp_matrix* lpA, int64_t n, const double* A,
                     int64_t lda, const double* b, const double* x0, int p, double tol,

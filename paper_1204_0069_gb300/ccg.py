@@ -26,6 +26,7 @@ EXPORTED = ["ccg_config_init", "ccg_create", "ccg_destroy", "ccg_solve", "ccg_so
             "ccg_server_config_init", "ccg_server_create", "ccg_server_submit", "ccg_server_poll",
             "ccg_server_stats", "ccg_server_destroy", "ccg_batch_tuning"]
 FP64, FP32_IR, BF16_IR, FP8_IR, FP64_SLICED = 0, 1, 2, 3, 4
+MIXED_AUTO, MIXED_REFINE, MIXED_PRECOND = 0, 1, 2
 NOALLOC_MAX_NP = 131072
 LOWP_BF16, LOWP_FP8_E4M3, LOWP_FP32, LOWP_FP64_SLICED = 0, 1, 2, 3
 
@@ -37,7 +38,9 @@ class Config(ctypes.Structure):
                 ("residual_replacement", ctypes.c_int),
                 ("barrier_timeout_ms", ctypes.c_double), ("max_ctas", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("explicit_residual", ctypes.c_int), ("batch_autotune", ctypes.c_int)]
+                ("explicit_residual", ctypes.c_int), ("batch_autotune", ctypes.c_int),
+                ("mixed_method", ctypes.c_int), ("cheb_degree", ctypes.c_int),
+                ("cheb_ratio", ctypes.c_double)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -186,7 +189,8 @@ class Solver:
                  x0_spread: float = 1.0, seed: int = 0, residual_replacement: bool = True,
                  barrier_timeout_ms: float = 10000.0, max_ctas: int = 0, precision: int = 0,
                  inner_tol: float = 0.0, max_outer: int = 0, explicit_residual: bool = False,
-                 batch_autotune: bool = True):
+                 batch_autotune: bool = True, mixed_method: int = 0, cheb_degree: int = 0,
+                 cheb_ratio: float = 0.0):
         L = lib()
         cfg = Config()
         L.ccg_config_init(ctypes.byref(cfg))
@@ -203,6 +207,9 @@ class Solver:
         cfg.max_outer = max_outer
         cfg.explicit_residual = int(bool(explicit_residual))
         cfg.batch_autotune = int(bool(batch_autotune))
+        cfg.mixed_method = int(mixed_method)
+        cfg.cheb_degree = int(cheb_degree)
+        cfg.cheb_ratio = float(cheb_ratio)
         h = _VP()
         rc = L.ccg_create(ctypes.byref(h), ctypes.byref(cfg))
         if rc != 0:

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -61,9 +62,25 @@ struct Buf {
   size_t bytes = 0;
 };
 
+// Policy and tensor-core kind of a quantised preconditioner matrix.
+int pre_policy(int format) {
+  return format == CCG_LOWP_FP8_E4M3 ? ccg::POL_FP8
+         : format == CCG_LOWP_FP32   ? ccg::POL_TF32X3
+                                     : ccg::POL_BF16;
+}
+int pre_kind(int format) {
+  return format == CCG_LOWP_FP8_E4M3 ? ccg::lp::KIND_FP8
+         : format == CCG_LOWP_FP32   ? ccg::lp::KIND_TF32X3
+                                     : ccg::lp::KIND_BF16;
+}
+
+// One FP64 solve.  With `pre` (a quantised copy of A) the solve is the
+// preconditioned form (CCG_MIXED_PRECOND): the persistent kernel yields
+// whenever it needs Z = q(A_lp) R, the Chebyshev launch writes Z, and the
+// solve resumes; its block products are formed from FP8 slices for p <= 16.
 int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const double* b,
                const double* x0, const double* X0, int p, double tol, int maxit, double* x_out,
-               double* X_out, ccg_result* res) {
+               double* X_out, ccg_result* res, const ccg_lowp_matrix_s* pre = nullptr) {
   if (res) {
     std::memset(res, 0, sizeof(*res));
     res->agent = -1;
@@ -73,7 +90,8 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
     return st;
   };
   if (!h || n < 1 || p < 1 || p > ccg::kMaxP || p > n || lda < n || !(tol > 0.0) ||
-      (h->cfg.precision == CCG_FP64_SLICED && p > 16) ||
+      (!pre && h->cfg.precision == CCG_FP64_SLICED && p > 16) ||
+      (pre && (pre->n != n || pre->device != h->device)) ||
       !std::isfinite(tol) || maxit < 0 || !A || !b || !x_out)
     return fail(CCG_ERR_INVALID);
   DeviceGuard guard(h->device);
@@ -101,9 +119,21 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
   if (rc != CCG_OK) return fail(rc);
 
   const int G = grid_size(h, n);
+  // preconditioner buffers: Z and the Chebyshev scratch blocks, the operand
+  // rows and partial tiles of the quantised product, the eigenvalue bound
+  const int P0 = ccg::p_bucket(p);
+  const int pre_NP = P0 <= 16 ? 16 : 32;
+  const int pre_kd = pre ? pre_kind(pre->format) : 0;
+  const size_t pre_esz = pre_kd == ccg::lp::KIND_BF16 ? 2 : pre_kd == ccg::lp::KIND_TF32X3 ? 4 : 1;
+  const int pre_NB = pre_kd == ccg::lp::KIND_BF16 ? pre_NP : 2 * pre_NP;
+  const int64_t ldk0 = ccg::lp::ld_elems(n);
+  const int64_t T0 = (n + 127) / 128;
   const size_t ws_need =
       Carve::need({5 * np * sizeof(double), (size_t)G * ccg::kPartStride * sizeof(double),
-                   sizeof(DevState)});
+                   sizeof(DevState), pre ? 4 * np * sizeof(double) : 0,
+                   pre ? (size_t)pre_NB * ldk0 * pre_esz : 0,
+                   pre ? (size_t)(G + T0) * 128 * pre_NP * sizeof(float) : 0,
+                   pre ? sizeof(unsigned long long) : 0});
   rc = ensure(&h->ws, &h->ws_bytes, ws_need);
   if (rc != CCG_OK) return fail(rc);
 
@@ -172,7 +202,7 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
 
   const int P = ccg::p_bucket(p);
   bool vec = (prm.lda % 2 == 0) && aligned(dA, 16);
-  const bool sliced = h->cfg.precision == CCG_FP64_SLICED;
+  const bool sliced = pre ? p <= 16 : h->cfg.precision == CCG_FP64_SLICED;
   const int pol = sliced ? ccg::POL_SLICED : ccg::POL_FP64;
   ccg_lowp_matrix_s* m = nullptr;
   if (sliced) {
@@ -237,10 +267,82 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
     return fail(CCG_ERR_CUDA);
   }
 
+  // Chebyshev preconditioner launches on the quantised A (MODE_CHEB): same
+  // grid, state and partial slots as the solve
+  Params cp{};
+  const int pre_pol = pre ? pre_policy(pre->format) : 0;
+  if (pre) {
+    cp = prm;
+    cp.mode = ccg::MODE_CHEB;
+    cp.V = prm.R;
+    cp.Z = wc.take<double>(np);
+    cp.cheb_d = wc.take<double>(np);
+    cp.cheb_s = wc.take<double>(np);
+    cp.cheb_w = wc.take<double>(np);
+    void* pdq = wc.take<char>((size_t)pre_NB * ldk0 * pre_esz);
+    float* ppart = wc.take<float>((size_t)(G + T0) * 128 * pre_NP);
+    auto* bound = wc.take<unsigned long long>(1);
+    cp.lp_kelems = (int)(128 / pre_esz);
+    cp.lp_kc = (int)((n + cp.lp_kelems - 1) / cp.lp_kelems);
+    cp.lp_tiles = T0;
+    cp.lp_units = T0 * cp.lp_kc;
+    cp.lp_row_scale = pre->row_scale;
+    cp.lp_dq = pdq;
+    cp.lp_ldk = ldk0;
+    cp.lp_part = ppart;
+    cp.cheb_steps = h->cfg.cheb_degree > 0 ? h->cfg.cheb_degree : 32;
+    const double ratio = h->cfg.cheb_ratio > 0.0 ? h->cfg.cheb_ratio : 3e-4;
+    prm.precond = 1;
+    prm.Z = cp.Z;
+    if (!ccg::lp::make_tensor_map(&cp.lp_tmA, pre->q, pre_kd, n, n, pre->ldq, 128) ||
+        !ccg::lp::make_tensor_map(&cp.lp_tmB, pdq, pre_kd, pre_NB, n, ldk0, pre_NB) ||
+        ccg::fp64_ctas_per_sm(P, true, pre_pol) < 1) {
+      release_sliced(h, m);
+      return fail(CCG_ERR_CUDA);
+    }
+    // operand rows beyond the active columns must read as zeros
+    e = cudaMemsetAsync(pdq, 0, (size_t)pre_NB * ldk0 * pre_esz, s);
+    if (e == cudaSuccess) e = ccg::lp::eig_bound(pre_kd, prm.A, prm.lda, n, bound, s);
+    unsigned long long hb = 0;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&hb, bound, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      release_sliced(h, m);
+      return fail(map_cuda(e));
+    }
+    double hi;
+    std::memcpy(&hi, &hb, sizeof(hi));
+    if (!(hi > 0.0) || !std::isfinite(hi)) {
+      release_sliced(h, m);
+      return fail(CCG_ERR_NUMERICAL);
+    }
+    cp.cheb_hi = hi;
+    cp.cheb_lo = ratio * hi;
+  }
+
   init_state(h->h_state, p);
+  int pc_apps = 0;
   e = cudaMemcpyAsync(prm.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev0, s);
   if (e == cudaSuccess) e = ccg::launch_fp64(prm, P, vec, G, s, pol);
+  if (pre) {
+    // the solve yields for each preconditioner application: read the state's
+    // leading words, run the Chebyshev launch, resume
+    constexpr size_t kHeadBytes = offsetof(DevState, keep);
+    Params rp = prm;
+    rp.resume = 1;
+    while (e == cudaSuccess) {
+      e = cudaMemcpyAsync(h->h_state, prm.st, kHeadBytes, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) break;
+      const DevState& hs = *h->h_state;
+      if (hs.error != 0 || hs.ctrl == ccg::CTRL_FINISH || hs.pc_stage == ccg::PC_NONE) break;
+      e = ccg::launch_fp64(cp, P, true, G, s, pre_pol);
+      if (e == cudaSuccess) e = ccg::launch_fp64(rp, P, vec, G, s, pol);
+      ++pc_apps;
+    }
+  }
   if (e == cudaSuccess) e = cudaEventRecord(h->ev1, s);
   release_sliced(h, m);
   if (e == cudaSuccess)
@@ -267,11 +369,28 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     res->device_ms = ms;
     res->ctas = G;
+    res->outer_steps = pc_apps;
   }
+  if (pre && status == CCG_OK && h->h_state->pc_stage != ccg::PC_NONE) status = CCG_ERR_CUDA;
   return status;
 }
 
 }  // namespace
+
+// The preconditioned mixed-precision solve (CCG_MIXED_PRECOND) for
+// ccg_solve_mixed: FP64 cCG on A with Chebyshev directions on lpA.
+int ccg_solve_precond(ccg_handle* h, const ccg_lowp_matrix* m, int64_t n, const double* A,
+                      int64_t lda, const double* b, const double* x0, int p, double tol,
+                      int maxit, double* x_out, ccg_result* res) {
+  if (!m || m->format == CCG_LOWP_FP64_SLICED) {
+    if (res) {
+      std::memset(res, 0, sizeof(*res));
+      res->status = CCG_ERR_INVALID;
+    }
+    return CCG_ERR_INVALID;
+  }
+  return solve_impl(h, n, A, lda, b, x0, nullptr, p, tol, maxit, x_out, nullptr, res, m);
+}
 
 extern "C" {
 
@@ -291,6 +410,9 @@ void ccg_config_init(ccg_config* cfg) {
   cfg->max_outer = 0;
   cfg->explicit_residual = 0;
   cfg->batch_autotune = 1;
+  cfg->mixed_method = CCG_MIXED_AUTO;
+  cfg->cheb_degree = 0;
+  cfg->cheb_ratio = 0.0;
 }
 
 int ccg_create(ccg_handle** out, const ccg_config* cfg) {
@@ -305,7 +427,10 @@ int ccg_create(ccg_handle** out, const ccg_config* cfg) {
       c.max_ctas < 0 || c.inner_tol < 0.0 || c.max_outer < 0 ||
       (c.explicit_residual != 0 && c.explicit_residual != 1) ||
       (c.batch_autotune != 0 && c.batch_autotune != 1) ||
-      (c.explicit_residual && c.precision != CCG_FP64))
+      (c.explicit_residual && c.precision != CCG_FP64) ||
+      (c.mixed_method != CCG_MIXED_AUTO && c.mixed_method != CCG_MIXED_REFINE &&
+       c.mixed_method != CCG_MIXED_PRECOND) ||
+      c.cheb_degree < 0 || c.cheb_degree > 1024 || !(c.cheb_ratio >= 0.0 && c.cheb_ratio < 1.0))
     return CCG_ERR_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess) {

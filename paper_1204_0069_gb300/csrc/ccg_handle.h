@@ -123,3 +123,9 @@ int lowp_create_async(ccg_handle* h, int format, int64_t n, const double* A, int
 void lowp_destroy_async(ccg_handle* h, ccg_lowp_matrix_s* m);
 
 }  // namespace ccg_host
+
+// Preconditioned mixed-precision solve (ccg_capi.cu), the CCG_MIXED_PRECOND
+// method of ccg_solve_mixed.
+int ccg_solve_precond(ccg_handle* h, const ccg_lowp_matrix* m, int64_t n, const double* A,
+                      int64_t lda, const double* b, const double* x0, int p, double tol,
+                      int maxit, double* x_out, ccg_result* res);

@@ -35,7 +35,17 @@ enum Mode : int {
   MODE_SOLVE = 0,
   MODE_BLOCK_PRODUCT = 1,
   MODE_BARRIER_SELFTEST = 2,
-  MODE_REFINE = 3      // x += c delta; r = b - A x (FP64); scaled residual
+  MODE_REFINE = 3,     // x += c delta; r = b - A x (FP64); scaled residual
+  MODE_CHEB = 4        // Z = q(A_lp) R: Chebyshev polynomial preconditioner
+};
+
+// Preconditioned FP64 solve (outer loop of the mixed-precision path): the
+// step the next launch resumes with once the preconditioner launch has
+// written Z = q(A_lp) R.
+enum PcStage : int {
+  PC_NONE = 0,
+  PC_SET_D = 1,   // D_k = Z (after the initial block or a residual replacement)
+  PC_BETA = 2     // H = Z'W, beta_k, D_{k+1} = Z + D_k beta_k^T
 };
 
 // A-pass policy of the persistent kernel: FP64 A on the FP64 pipe, a
@@ -76,7 +86,9 @@ struct DevState {
   int k_replaced;           // iteration count at the last replacement
   int zero_rhs;             // b == 0
   int err_where;            // diagnostic: phase that set `error`
-  int pad0;
+  int pc_stage;             // PcStage: preconditioned solve waits for Z
+  int cur;                  // preconditioned solve: current direction buffer (0: D0)
+  int pad1;
   int keep[kMaxP];          // kept columns (pre-compaction indices)
   int agent[kMaxP];         // original agent id of each active column
   int old_agent[kMaxP];     // agent ids before the last compaction
@@ -171,6 +183,19 @@ struct Params {
   double ref_coef;
   double* ref_r;           // A x - b
   double* ref_bin;         // -(A x - b) * sqrt(n) / ||b - A x||
+  // preconditioned FP64 solve: D_{k+1} = Z_{k+1} + D_k beta_k^T with
+  // Z = q(A_lp) R written by a MODE_CHEB launch between two launches of the
+  // solve (resume = 1 continues from the state in st)
+  int precond;
+  int resume;
+  double* Z;               // n x p, leading dimension p
+  // MODE_CHEB: scratch blocks (n x p each) and the polynomial
+  double* cheb_d;
+  double* cheb_s;
+  double* cheb_w;
+  int cheb_steps;          // products with A_lp per application
+  double cheb_lo;          // interval [cheb_lo, cheb_hi] of the Chebyshev polynomial
+  double cheb_hi;
   CUtensorMap lp_tmA;  // A_lp tiles (the type carries its alignment)
   CUtensorMap lp_tmB;  // operand tiles
 };

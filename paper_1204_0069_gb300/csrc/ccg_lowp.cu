@@ -279,6 +279,44 @@ __global__ void quant_fp8_kernel(const double* __restrict__ A, int64_t lda, int6
   }
 }
 
+// Bound on the largest eigenvalue of a quantised copy A_q of A (Gershgorin):
+// max_i [(1 + rel) sum_k |A_ik| + n absf max_k |A_ik|], where every entry of
+// A_q satisfies |A_q,ik| <= (1 + rel) |A_ik| + absf max_k |A_ik| (rel: the
+// format's relative rounding, absf: its absolute rounding below the normal
+// range relative to the row scale).  Folded into *out with atomicMax on the
+// bits of the non-negative double (they order as the values).  One block per
+// row.
+__global__ void eig_bound_kernel(const double* __restrict__ A, int64_t lda, int64_t n,
+                                 double rel, double absf, unsigned long long* __restrict__ out) {
+  __shared__ double red[2][32];
+  const int64_t i = blockIdx.x;
+  double t = 0.0, m = 0.0;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+    const double a = fabs(A[i * lda + k]);
+    t += a;
+    m = fmax(m, a);
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = t;
+    red[1][threadIdx.x >> 5] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0, mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      r += red[0][w];
+      mx = fmax(mx, red[1][w]);
+    }
+    // the sum of n non-negative terms is at most (1 + n 2^-52) too small
+    const double b = ((1.0 + rel) * r + (double)n * absf * mx) * (1.0 + (double)n * 0x1.0p-51);
+    atomicMax(out, (unsigned long long)__double_as_longlong(b));
+  }
+}
+
 // A (FP64) -> kSlices FP8 slices without rounding error (the error-free
 // splitting of Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
 // matrix multiplication by using fast routines of matrix multiplication and
@@ -420,6 +458,19 @@ size_t part_floats(int64_t n, int ctas, int NP) {
 }
 
 int64_t slice_rows(int64_t n) { return (n + kBM - 1) / kBM * kBM; }
+
+cudaError_t eig_bound(int kind, const double* A, int64_t lda, int64_t n,
+                      unsigned long long* out, cudaStream_t s) {
+  // relative rounding of the format and its absolute rounding below the
+  // normal range (FP8 E4M3 with row scale s_i = max/448: half the smallest
+  // subnormal step, 2^-10 s_i < 2^-18 max)
+  const double rel = kind == KIND_FP8 ? 0x1.0p-4 : kind == KIND_BF16 ? 0x1.0p-8 : 0x1.0p-20;
+  const double absf = kind == KIND_FP8 ? 0x1.0p-18 : 0.0;
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  eig_bound_kernel<<<(unsigned)n, 256, 0, s>>>(A, lda, n, rel, absf, out);
+  return cudaGetLastError();
+}
 static_assert(kSlicesHost == kSlices, "slice count");
 
 cudaError_t quantize(int kind, const double* A, int64_t lda, int64_t n, void* Q, int64_t ldq,

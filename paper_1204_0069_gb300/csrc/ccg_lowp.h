@@ -37,6 +37,11 @@ size_t part_floats(int64_t n, int ctas, int NP);
 // of ldq bytes, with one power-of-two scale per row (row_scale).
 cudaError_t quantize(int kind, const double* A, int64_t lda, int64_t n, void* Q, int64_t ldq,
                      float* row_scale, cudaStream_t s);
+// Upper bound on the eigenvalues of the copy of A quantised to `kind`
+// (Gershgorin on the FP64 A with the format's rounding), as the bits of a
+// double in *out (device memory).
+cudaError_t eig_bound(int kind, const double* A, int64_t lda, int64_t n,
+                      unsigned long long* out, cudaStream_t s);
 // Rows of one slice of the sliced FP64 format (n rounded up to 128).
 int64_t slice_rows(int64_t n);
 // V (FP64, n x q row-major) -> Vt: NP (BF16) or 2 NP (FP8 hi, lo) rows of ldk

@@ -1,6 +1,8 @@
 // ccg_mixed.cu -- mixed-precision solve (include/ccg.h: ccg_solve_mixed).
 //
-// FP64 iterative refinement around inner cCG solves on a quantised A:
+// CCG_MIXED_PRECOND goes to the preconditioned FP64 solve (ccg_capi.cu);
+// CCG_MIXED_REFINE is FP64 iterative refinement around inner cCG solves on a
+// quantised A:
 //   x = x0;  r = b - A x (FP64, MODE_REFINE)
 //   repeat:  solve A_lp d = r_s with p agents to a loose relative tolerance,
 //            where r_s = r sqrt(n) / ||r|| (unit-RMS right-hand side, so the
@@ -66,6 +68,13 @@ extern "C" int ccg_solve_mixed(ccg_handle* h, const ccg_lowp_matrix* m, int64_t 
     if (res) res->status = st;
     return st;
   };
+  if (h && m) {
+    const int method = h->cfg.mixed_method != CCG_MIXED_AUTO ? h->cfg.mixed_method
+                       : m->format == CCG_LOWP_FP32          ? CCG_MIXED_REFINE
+                                                             : CCG_MIXED_PRECOND;
+    if (method == CCG_MIXED_PRECOND)
+      return ccg_solve_precond(h, m, n, A, lda, b, x0, p, tol, maxit, x_out, res);
+  }
   if (!h || !m || n < 1 || m->n != n || m->device != h->device || p < 1 || p > ccg::kMaxP ||
       p > n || lda < n || !(tol > 0.0) || !std::isfinite(tol) || maxit < 0 || !A || !b || !x_out)
     return fail(CCG_ERR_INVALID);

@@ -68,8 +68,9 @@ struct ccg_server_s {
 namespace {
 
 // Device bytes a request holds while it runs: its matrix (resident for the
-// request's lifetime), the quantised copy of the mixed-precision path, and
-// the solver workspace (blocks, partial sums, operand rows, partial tiles).
+// request's lifetime), the quantised copy of the mixed-precision path (and,
+// for BF16 / FP8, the sliced copy of the preconditioned FP64 solve), and the
+// solver workspace (blocks, partial sums, operand rows, partial tiles).
 double reservation(const ccg_server_config& c, int64_t n, int64_t lda, int p, int shares) {
   const double a = (double)n * (double)lda * 8.0;
   const double ld = (double)((n + 127) / 128 * 128);
@@ -77,8 +78,14 @@ double reservation(const ccg_server_config& c, int64_t n, int64_t lda, int p, in
   if (c.precision == CCG_FP32_IR) lp = (double)n * ld * 4.0 + 64.0 * ld * 4.0;
   else if (c.precision == CCG_BF16_IR) lp = (double)n * ld * 2.0 + 32.0 * ld * 2.0;
   else if (c.precision == CCG_FP8_IR) lp = (double)n * ld * 1.0 + 64.0 * ld + 4.0 * n;
-  else if (c.precision == CCG_FP64_SLICED)  // 14 slices, operand slices, FP64 partial tiles
-    lp = 14.0 * ld * ld + 4.0 * n + 224.0 * ld + (shares + ld / 128.0) * 128.0 * p * 8.0;
+  const double sliced =
+      14.0 * ld * ld + 4.0 * n + 224.0 * ld + (shares + ld / 128.0) * 128.0 * p * 8.0;
+  if (c.precision == CCG_FP64_SLICED)  // 14 slices, operand slices, FP64 partial tiles
+    lp = sliced;
+  else if (c.precision == CCG_BF16_IR || c.precision == CCG_FP8_IR)
+    // the preconditioned FP64 solve (the default method for BF16 / FP8) also
+    // holds the sliced copy and four more n x p blocks
+    lp += (p <= 16 ? sliced : 0.0) + 4.0 * n * p * 8.0;
   const double ws = 5.0 * n * p * 8.0 + shares * ccg::kPartStride * 8.0 + 6.0 * n * 8.0 +
                     (double)(shares + (n + 127) / 128) * 128.0 * 32.0 * 4.0 + 65536.0;
   return a + lp + ws;

@@ -1043,6 +1043,71 @@ __device__ void serial_beta(const Params& prm, SerialSmem& S) {
   stop_test(prm, S, pk, 7);
 }
 
+// Preconditioned solve, after the update of X and R: iteration count and
+// stop test on the residual norms (beta_k follows once Z_{k+1} is known).
+__device__ void serial_kstop(const Params& prm, SerialSmem& S) {
+  DevState* st = prm.st;
+  const int pk = ldcg(&st->pk);
+  for (int e = threadIdx.x; e < pk; e += kThreads) S.s2[e] = red_get(st, kSlotVec + e);
+  if (threadIdx.x == 0) st->k = ldcg(&st->k) + 1;
+  __syncthreads();
+  stop_test(prm, S, pk, 17);
+}
+
+// Preconditioned solve: beta_k^T = -M^{-1} H^T with H = Z_{k+1}' A D_k in the
+// Gram0 slot, from the factor of M kept by the alpha step.
+template <int NB>
+__device__ void serial_beta_pc(const Params& prm, SerialSmem& S) {
+  DevState* st = prm.st;
+  const int tid = threadIdx.x;
+  const int pk = ldcg(&st->pk);
+  const int sq = pk * pk;
+  if (tid < 4) S.flag[tid] = 0;
+  for (int e = tid; e < sq; e += kThreads) {
+    const int a = e / pk, c = e - a * pk;
+    S.g[a * kLd + c] = red_get(st, kSlotGram0 + a * kMaxP + c);
+    S.m[a * kLd + c] = ldcg(&st->L[a * kMaxP + c]);
+  }
+  if (tid < pk) S.sc[tid] = ldcg(&st->sc[tid]);
+  __syncthreads();
+  for (int e = tid; e < sq; e += kThreads) {
+    const int a = e / pk, c = e - a * pk;
+    if (!finite(S.g[a * kLd + c])) S.flag[0] = 1;
+    S.l[a * kLd + c] = S.sc[a] * S.g[c * kLd + a];
+  }
+  __syncthreads();
+  if (S.flag[0]) {
+    if (tid == 0) set_error(st, ST_ERR_NUMERICAL, 18);
+    __syncthreads();
+    return;
+  }
+  chol_solve_cols<NB>(S.m, S.l, pk, S.sv);
+  for (int e = tid; e < sq; e += kThreads) {
+    const int b = e / pk, a = e - b * pk;
+    const double v = -S.sc[b] * S.l[b * kLd + a];
+    st->betaT[b * kMaxP + a] = v;
+    if (!finite(v)) S.flag[1] = 1;
+  }
+  if (tid == 0) st->pc_stage = PC_NONE;
+  __syncthreads();
+  if (S.flag[1] && tid == 0) set_error(st, ST_ERR_NUMERICAL, 19);
+  __syncthreads();
+}
+
+// Preconditioned solve: after a stop test that continues the iteration, wait
+// for Z (the launch ends and the preconditioner runs).
+__device__ void serial_pc_request(const Params& prm, int stage) {
+  if (!prm.precond) return;
+  DevState* st = prm.st;
+  if (threadIdx.x == 0 && *(volatile int*)&st->error == 0 && ldcg(&st->ctrl) == CTRL_LOOP)
+    st->pc_stage = stage;
+  __syncthreads();
+}
+__device__ void serial_pc_clear(const Params& prm) {
+  if (prm.precond && threadIdx.x == 0) prm.st->pc_stage = PC_NONE;
+  __syncthreads();
+}
+
 __device__ void serial_bnorm(const Params& prm, SerialSmem& S) {
   DevState* st = prm.st;
   if (threadIdx.x == 0) {
@@ -1777,6 +1842,53 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
           st->result = ST_OK;
         return;
       }
+      if constexpr (POL != POL_SLICED) {
+        if (prm.mode == MODE_CHEB) {
+          // Preconditioner of the FP64 solve: Z = q(A_lp) R, the Chebyshev
+          // iteration for A_lp Z = R from Z = 0 on [lo, hi], cheb_steps
+          // products with the quantised A (Saad, Iterative Methods for Sparse
+          // Linear Systems, Sec. 12.3: Chebyshev acceleration).  The same
+          // polynomial for every column; no inner products, so no reductions.
+          if (tid == 0) s_int[1] = ldcg(&st->pk);
+          __syncthreads();
+          const int pk = s_int[1];
+          const double th = 0.5 * (prm.cheb_hi + prm.cheb_lo);
+          const double de = 0.5 * (prm.cheb_hi - prm.cheb_lo);
+          const double sg = th / de;
+          double rho = 1.0 / sg;
+          double* Z = prm.Z;
+          double* d = prm.cheb_d;
+          double* sr = prm.cheb_s;
+          const int64_t cnt = (r1 - r0) * pk;
+          for (int64_t idx = tid; idx < cnt; idx += kThreads) {
+            const int64_t o = (r0 + idx / pk) * p + idx % pk;
+            const double r = ldcg(prm.V + o);
+            const double v = r / th;
+            d[o] = v;
+            Z[o] = v;
+            sr[o] = r;
+          }
+          __syncthreads();
+          for (int k = 1; k < prm.cheb_steps; ++k) {
+            // W = A_lp d ; S -= W ; d = c1 d + c2 S ; Z += d
+            if (!lp_apass<P, POL>(prm, d, pk, prm.cheb_w, false, r0, r1, *L, &ss, &s_err))
+              return;
+            const double rn = 1.0 / (2.0 * sg - rho);
+            const double c1 = rn * rho, c2 = 2.0 * rn / de;
+            for (int64_t idx = tid; idx < cnt; idx += kThreads) {
+              const int64_t o = (r0 + idx / pk) * p + idx % pk;
+              const double sv = sr[o] - ldcg(prm.cheb_w + o);
+              const double dv = c1 * d[o] + c2 * sv;
+              sr[o] = sv;
+              d[o] = dv;
+              Z[o] += dv;
+            }
+            rho = rn;
+            __syncthreads();
+          }
+          return;
+        }
+      }
     }
     // inner solves only, except the sliced FP64 policy: a full FP64 solve
     if (prm.mode != MODE_SOLVE || (!prm.skip_true_check && POL != POL_SLICED)) {
@@ -1785,6 +1897,21 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     }
   }
 
+  // Preconditioned FP64 solve: a serial step that leaves the solve waiting
+  // for Z = q(A_lp) R sets st->pc_stage; every CTA then records the direction
+  // buffer and leaves, and the next launch (resume = 1) continues.
+  const bool pc = kExact && prm.precond;
+#define CCG_PC_YIELD(CUR)                                                    \
+  if (pc) {                                                                  \
+    if (tid == 0) s_int[3] = ldcg(&st->pc_stage);                            \
+    __syncthreads();                                                         \
+    if (s_int[3] != PC_NONE) {                                               \
+      if (tid == 0 && cta == 0) st->cur = (CUR);                             \
+      return;                                                                \
+    }                                                                        \
+  }
+
+  if (!prm.resume) {
   // ---- initial block X_0 and ||b|| ----
   for (int64_t idx = r0 * p + tid; idx < r1 * p; idx += kThreads) {
     const int64_t i = idx / p;
@@ -1820,10 +1947,23 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     }
     for (int64_t idx = r0 * p + tid; idx < r1 * p; idx += kThreads) prm.D0[idx] = ldcg(prm.R + idx);
     partial_grams<POL == POL_FP64 || POL == POL_SLICED>(nullptr, nullptr, nullptr, nullptr, prm.R, p, p, r0, r1, mypart, smem, kStageDoubles);
-    CCG_SYNC_RED(RED_S, p, serial_norms(prm, S, false));
+    CCG_SYNC_RED(RED_S, p, (serial_norms(prm, S, false), serial_pc_request(prm, PC_SET_D)));
+    CCG_PC_YIELD(0);
+  }
   }
 
   int cur = 0;
+  // a resumed launch starts with the step its predecessor left waiting for Z
+  int pc_stage = PC_NONE;
+  if (prm.resume) {
+    if (tid == 0) {
+      s_int[0] = ldcg(&st->cur);
+      s_int[1] = ldcg(&st->pc_stage);
+    }
+    __syncthreads();
+    cur = s_int[0];
+    pc_stage = s_int[1];
+  }
   // BF16 / TF32 inner solves: the D-update writes D_{k+1} in the MMA type too,
   // and the next tensor-core A-pass skips its conversion and barrier
   constexpr bool kFuseConv = POL == POL_BF16 || POL == POL_TF32X3;
@@ -1838,6 +1978,43 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     int pk = s_int[1];
     double* D = cur ? prm.D1 : prm.D0;
     double* Dn = cur ? prm.D0 : prm.D1;
+
+    if (pc && pc_stage != PC_NONE && ctrl == CTRL_LOOP) {
+      const int stage = pc_stage;
+      pc_stage = PC_NONE;
+      if (stage == PC_SET_D) {
+        // D_k = Z_k (after the initial block or a residual replacement); the
+        // serial step of the next exchange clears st->pc_stage
+        for (int64_t idx = tid; idx < (r1 - r0) * pk; idx += kThreads) {
+          const int64_t o = (r0 + idx / pk) * p + idx % pk;
+          D[o] = ldcg(prm.Z + o);
+        }
+        if (!grid_barrier(prm, &ss, &s_err)) return;
+      } else {
+        // H = Z_{k+1}' A D_k ; beta_k^T = -M^{-1} H^T ; D_{k+1} = Z_{k+1} + D_k beta_k^T
+        partial_grams<true>(prm.Z, prm.W, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart, smem,
+                            kStageDoubles);
+        CCG_SYNC_RED(RED_H_S, pk, serial_beta_pc<P>(prm, S));
+        double* Ts = smem;
+        for (int e = tid; e < pk * pk; e += kThreads) {
+          const int b = e / pk, a = e - b * pk;
+          Ts[b * kLd + a] = ldcg(&st->betaT[b * kMaxP + a]);
+        }
+        __syncthreads();
+        const int64_t cnt = (r1 - r0) * pk;
+        for (int64_t idx = tid; idx < cnt; idx += kThreads) {
+          const int64_t i = r0 + idx / pk;
+          const int a = (int)(idx % pk);
+          double acc = 0.0;
+#pragma unroll 8
+          for (int b = 0; b < pk; ++b) acc = fma(ldcg(D + i * p + b), Ts[b * kLd + a], acc);
+          Dn[i * p + a] = ldcg(prm.Z + i * p + a) + acc;
+        }
+        if (!grid_barrier(prm, &ss, &s_err)) return;
+        cur ^= 1;
+      }
+      continue;
+    }
 
     if (ctrl == CTRL_FINISH) {
       const int zero = ldcg(&st->zero_rhs);
@@ -1885,7 +2062,8 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         if (c < pk) D[idx] = ldcg(prm.R + idx);
       }
       partial_grams<POL == POL_FP64 || POL == POL_SLICED>(nullptr, nullptr, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart, smem, kStageDoubles);
-      CCG_SYNC_RED(RED_S, pk, serial_norms(prm, S, true));
+      CCG_SYNC_RED(RED_S, pk, (serial_norms(prm, S, true), serial_pc_request(prm, PC_SET_D)));
+      CCG_PC_YIELD(cur);
       continue;
     }
 
@@ -1899,7 +2077,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         return;
     }
     partial_grams<POL == POL_FP64 || POL == POL_SLICED>(D, prm.W, prm.R, D, nullptr, p, pk, r0, r1, mypart, smem, kStageDoubles);
-    CCG_SYNC_RED(RED_M_G, pk, (serial_alpha<P, !kExact>(prm, S)));
+    CCG_SYNC_RED(RED_M_G, pk, (serial_alpha<P, !kExact>(prm, S), serial_pc_clear(prm)));
 
     if (tid == 0) {
       s_int[2] = ldcg(&st->changed);
@@ -1966,6 +2144,14 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         }
       }
     }
+    if (pc) {
+      // residual norms and the stop test now; beta_k once Z_{k+1} is there
+      partial_grams<true>(nullptr, nullptr, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart, smem,
+                          kStageDoubles);
+      CCG_SYNC_RED(RED_S, pk, (serial_kstop(prm, S), serial_pc_request(prm, PC_BETA)));
+      CCG_PC_YIELD(cur);
+      continue;
+    }
     partial_grams<POL == POL_FP64 || POL == POL_SLICED>(prm.R, prm.W, nullptr, nullptr, prm.R, p, pk, r0, r1, mypart, smem, kStageDoubles);
     CCG_SYNC_RED(RED_H_S, pk, serial_beta<P>(prm, S));
 
@@ -2005,6 +2191,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
       cur ^= 1;
     }
   }
+#undef CCG_PC_YIELD
 #undef CCG_SYNC_RED
 }
 
