@@ -5,14 +5,23 @@ One step = one complete FP64 cCG solve (initial residual, iterations to
 relative residual 1e-10, true-residual check, copy-out) of the dense SPD
 system A x = b with A the exponential kernel exp(-|z_i - z_j| / 0.2) on 8192
 points uniform in [0, 1]^3 (seed 1) plus 1e-2 I, b ~ N(0, 1), x0 = 0, p = 8
-agents.  The metric is solves/s.
+agents.  The metric is solves/s.  By default the solve forms its block
+products A D_k exactly on the FP8 tensor cores from 4-bit slices of A and D_k
+(CCG_FP64_SLICED: FP64 accuracy, parity-tested against the FP64 oracle);
+``--product fp64`` runs them on the FP64 pipe instead.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--p P] [--impl ours|reference]
 
 N > 1 runs independent replicas (one solve per rank per step; the method has
 no cross-GPU data path), launched by torchrun.
-``--impl reference`` times the FP64 CPU oracle on the host cores instead
-(bounded sample of iterations, scaled to a full solve).
+``--impl reference`` times the FP64 CPU oracle on the host cores instead: each
+timed step is one full oracle solve of the same system (warm-up steps are
+short samples).
+
+Output: one JSON line per additional measurement ({"detail": ...}: agent
+sweeps, the precision workload, tensor-core block products, batching,
+serving), then the result line, kept short, whose "targets" key collects the
+figures the method's targets rest on.
 """
 from __future__ import annotations
 
@@ -30,15 +39,25 @@ sys.path.insert(0, ROOT)
 
 N_DEFAULT = 8192
 TOL = 1e-10
-WORKLOAD = ("plain FP64 cCG: A = exp(-|z_i-z_j|/0.2) + 1e-2 I on n=8192 points U[0,1]^3 "
-            "(seed 1), b ~ N(0,1), x0 = 0, tol 1e-10 relative")
+WORKLOAD = ("FP64 cCG: A = exp(-|z_i-z_j|/0.2) + 1e-2 I on n=8192 points U[0,1]^3 (seed 1), "
+            "b ~ N(0,1), x0 = 0, tol 1e-10 relative")
 METRIC = "solves/s at relres 1e-10 (FP64 cCG)"
 GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
-# DRAM bytes (read + write) per pass over A of the persistent FP64 solve kernel,
-# measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a
-# 20-iteration solve of the benchmark system: 22 passes, 11 853.2 MB.  The
-# traffic grows with the passes, so a full solve is scaled from it.
-NCU_BYTES_PER_PASS = {(8192, 8): (11814291712 + 45762304) / 22.0}
+# DRAM bytes (read + write) per pass over A of the persistent solve kernels,
+# measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on
+# 20-iteration solves of the benchmark system (22 passes; the traffic grows
+# with the passes, so a full solve is scaled from it).  FP64 pipe, p = 8:
+# 11 853.2 MB; sliced product: see profiles/sliced_fp64_solve_traffic_n8192.md.
+NCU_BYTES_PER_PASS = {("fp64", 8192, 8): (11814291712 + 45762304) / 22.0}
+
+
+def run_config(n, p, product):
+    """The config dict both arms print (same workload, same keys)."""
+    return {"workload": WORKLOAD, "n": n, "p": p, "tol": TOL,
+            "product": "FP64 from exact FP8 slices (tensor cores)" if product == "sliced"
+                       else "FP64 pipe",
+            "l2": "inputs > L2 (A 512 MiB)",
+            "parallelism": "replicas"}
 
 
 def parse():
@@ -48,6 +67,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--product", default="sliced", choices=["sliced", "fp64"],
+                    help="block product of the timed FP64 solve")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -58,7 +79,8 @@ def parse():
                     choices=["none", "solve", "block", "lowp", "mixed", "lowp32", "sliced"],
                     help="profiling mode: run only K solves, K FP64 block products or K "
                          "tensor-core block products (n = 32768)")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision lines")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the additional measurements (sweeps, precision, batching, serving)")
     ap.add_argument("--lowp-n", type=int, default=32768,
                     help="size of the tensor-core block-product measurement")
     ap.add_argument("--lowp-fmt", default="bf16", choices=["bf16", "fp8"],
@@ -78,7 +100,9 @@ def workload(n):
     return wl.exp_kernel(n, seed=1, length=0.2, nugget=1e-2)
 
 
-def oracle_full_iterations(n, p):
+def oracle_golden_iterations(n, p):
+    """The oracle's iteration count on the benchmark system, as stored by
+    tests/golden/make_oracle_iterations.py (inputs generated on an x86 host)."""
     try:
         rows = json.load(open(GOLDEN_ITERS))["rows"]
     except (OSError, ValueError, KeyError):
@@ -89,9 +113,23 @@ def oracle_full_iterations(n, p):
     return None
 
 
+def cpu_full_solve(A, b, p):
+    """One full oracle solve on all host cores.  Returns (seconds, cores,
+    iterations)."""
+    import oracle
+    n = b.shape[0]
+    cores = os.cpu_count() or 1
+    X0 = oracle.initial_block(n, p, None, 1.0, 0)
+    t0 = time.perf_counter()
+    r = oracle.ccg(A, b, X0, TOL, 20 * n, nthreads=cores)
+    return time.perf_counter() - t0, cores, r["iterations"]
+
+
 def cpu_sample(A, b, p, target_s):
     """Time a bounded sample of oracle iterations on all host cores and scale
-    it to one full solve.  Returns (solves_per_s, cores, sample_text)."""
+    it to one full solve with the oracle's own iteration count (from a run of
+    the first sample to the end when target_s allows, else the stored count).
+    Returns (solves_per_s, cores, sample_text)."""
     import oracle
     n = b.shape[0]
     cores = os.cpu_count() or 1
@@ -103,17 +141,17 @@ def cpu_sample(A, b, p, target_s):
     t0 = time.perf_counter()
     oracle.ccg(A, b, X0, 1e-300, m, residual_replacement=False, nthreads=cores)
     tm = time.perf_counter() - t0
-    full = oracle_full_iterations(n, p)
+    full = oracle_golden_iterations(n, p)
     per_it = (tm - t2) / max(m - 2, 1)
     fixed = max(t2 - 2 * per_it, 0.0)      # init A X_0 + final true residual
     if full is None:
         full = m
         note = "full iteration count unknown: scaled to the sample length"
     else:
-        note = f"scaled to the oracle's full solve of {full} iterations"
+        note = f"scaled to its stored count of {full}"
     t_solve = fixed + per_it * full
-    return 1.0 / t_solve, cores, (f"first {m} oracle iterations (n={n}, p={p}, {tm:.1f} s on "
-                                  f"{cores} threads), {note}")
+    return 1.0 / t_solve, cores, (f"{m} oracle iterations ({tm:.1f} s, {cores} threads), "
+                                  f"{note}")
 
 
 class ClockSampler:
@@ -266,15 +304,16 @@ def lowp_roofline(ccg, solver, dev, A, p, hbm_gbs, steps=10):
 
 
 def mixed_lines(ccg, dev, stream, A, b, p, steps, tol=TOL):
-    """solves/s of FP64 cCG and of the two mixed-precision solves on (A, b)."""
+    """solves/s of FP64 cCG (FP64 pipe and sliced product) and of the
+    mixed-precision solves (default methods) on (A, b)."""
     import numpy as np
     import torch
     n = b.shape[0]
     dA = torch.from_numpy(A).to(dev)
     db = torch.from_numpy(b).to(dev)
     out = {}
-    for name, prec in [("fp64", ccg.FP64), ("fp32_ir", ccg.FP32_IR), ("bf16_ir", ccg.BF16_IR),
-                       ("fp8_ir", ccg.FP8_IR)]:
+    for name, prec in [("fp64_pipe", ccg.FP64), ("fp64_sliced", ccg.FP64_SLICED),
+                       ("fp32", ccg.FP32_IR), ("bf16", ccg.BF16_IR), ("fp8", ccg.FP8_IR)]:
         x = torch.zeros(n, dtype=torch.float64, device=dev)
         with ccg.Solver(stream=stream.cuda_stream, precision=prec) as s:
             s.solve(dA, db, x, p=p, tol=tol, maxit=20 * n)      # warm-up
@@ -292,9 +331,12 @@ def mixed_lines(ccg, dev, stream, A, b, p, steps, tol=TOL):
         out[name] = {"solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t, "status": r.status_name,
                      "relres_true": relres, "iterations": r.iterations,
                      "outer_steps": r.outer_steps}
-    for k in ("fp32_ir", "bf16_ir", "fp8_ir"):
-        out[f"speedup_{k}_vs_fp64"] = (out[k]["solves_per_s"] / out["fp64"]["solves_per_s"]
-                                       if out[k]["status"] == "CCG_OK" else None)
+    for k in ("fp32", "bf16", "fp8"):
+        ok = out[k]["status"] == "CCG_OK"
+        out[k]["speedup_vs_fp64_pipe"] = (out[k]["solves_per_s"] / out["fp64_pipe"]["solves_per_s"]
+                                          if ok else None)
+        out[k]["speedup_vs_fp64_sliced"] = (out[k]["solves_per_s"] /
+                                            out["fp64_sliced"]["solves_per_s"] if ok else None)
     return out
 
 
@@ -326,12 +368,25 @@ def p_sweep(ccg, solver, stream, dA, db, x, n, ps=(1, 4, 8, 16, 32)):
     return out
 
 
+PRECISION_METHODS = [
+    # name, precision, solver options, repetitions
+    ("fp64_pipe", 0, {}, 1),
+    ("fp64_sliced", 4, {}, 2),
+    ("fp32_refine", 1, {"mixed_method": 1}, 2),
+    ("fp32_precond", 1, {"mixed_method": 2}, 2),
+    ("bf16_precond", 2, {"mixed_method": 2}, 2),
+    ("fp8_precond", 3, {"mixed_method": 2}, 2),
+    ("bf16_refine", 2, {"mixed_method": 1, "max_outer": 12}, 1),
+    ("fp8_refine", 3, {"mixed_method": 1, "max_outer": 12}, 1),
+]
+
+
 def precision_lines(ccg, stream, A, p=16, tol=TOL, seed=2):
     """The precision workload at full size: A (FP64, on the device) is the
     exponential kernel on n points (length 0.1, nugget 1e-3), b ~ N(0, 1);
-    FP64 cCG, then FP32 / BF16 / FP8 A inside FP64 refinement.  Each line
-    states its true relative residual and its distance to the FP64 solution."""
-    import numpy as np
+    FP64 cCG (FP64 pipe and sliced product), then A in FP32 / BF16 / FP8 by
+    refinement and by the preconditioned FP64 solve.  Each line states its
+    true relative residual and its distance to the FP64 (FP64-pipe) answer."""
     import torch
     n = A.shape[0]
     dev = A.device
@@ -342,12 +397,9 @@ def precision_lines(ccg, stream, A, p=16, tol=TOL, seed=2):
     out = {"workload": f"exponential kernel, n = {n} points U[0,1]^3 (seed {seed}), length 0.1, "
                        f"nugget 1e-3, b ~ N(0,1), p = {p}, tol {tol}", "n": n, "p": p}
     x64 = None
-    for name, prec, reps in [("fp64", ccg.FP64, 1), ("fp64_sliced", ccg.FP64_SLICED, 2),
-                             ("fp32_ir", ccg.FP32_IR, 2), ("bf16_ir", ccg.BF16_IR, 1),
-                             ("fp8_ir", ccg.FP8_IR, 1)]:
+    for name, prec, opts, reps in PRECISION_METHODS:
         x = torch.zeros(n, dtype=torch.float64, device=dev)
-        with ccg.Solver(stream=stream.cuda_stream, precision=prec,
-                        max_outer=0 if prec in (ccg.FP64, ccg.FP32_IR) else 12) as s:
+        with ccg.Solver(stream=stream.cuda_stream, precision=prec, **opts) as s:
             s.solve(A, b, x, p=p, tol=tol, maxit=2)  # warm-up (kernels, workspace)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -368,10 +420,35 @@ def precision_lines(ccg, stream, A, p=16, tol=TOL, seed=2):
             line["err_vs_fp64"] = float(torch.linalg.vector_norm(x - x64) /
                                         torch.linalg.vector_norm(x64))
         out[name] = line
-    for k in ("fp64_sliced", "fp32_ir", "bf16_ir", "fp8_ir"):
-        out[f"speedup_{k}_vs_fp64"] = (out[k]["solves_per_s"] / out["fp64"]["solves_per_s"]
-                                       if out[k]["status"] == "CCG_OK" else None)
+    for k, _, _, _ in PRECISION_METHODS[1:]:
+        ok = out[k]["status"] == "CCG_OK"
+        out[k]["speedup_vs_fp64_pipe"] = (out[k]["solves_per_s"] / out["fp64_pipe"]["solves_per_s"]
+                                          if ok else None)
+        out[k]["speedup_vs_fp64_sliced"] = (out[k]["solves_per_s"] /
+                                            out["fp64_sliced"]["solves_per_s"] if ok else None)
     return out
+
+
+def fp64_dgemm_tflops(dev, n=8192, reps=5):
+    """FP64 rate of this GPU as cuBLAS DGEMM reaches it (torch.matmul,
+    2 n^3 flops, best of reps): the measured FP64 peak of the roofline."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
 
 
 def batched_line(ccg, dev, stream, count=4096, p=4, seed=3):
@@ -463,29 +540,37 @@ def serving_line(ccg, dev, precision, count=48, rate=2000.0, seed=4, workers=8):
 
 
 def run_reference(args, rank, world):
+    """The oracle arm: warm-up steps time short samples; each timed step is one
+    full FP64 oracle solve of the benchmark system on the host cores."""
     if rank != 0:
         return
     A, b = workload(args.n)
-    per_step = max(2.0, args.cpu_seconds / max(args.steps, 1))
-    vals = []
-    info = None
-    for i in range(args.warmup + args.steps):
-        v, cores, sample = cpu_sample(A, b, args.p, per_step)
-        if i >= args.warmup:
-            vals.append(v)
-            info = (cores, sample)
-    value = statistics.mean(vals)
+    for _ in range(args.warmup):
+        cpu_sample(A, b, args.p, 1.0)
+    secs, its = [], None
+    cores = os.cpu_count() or 1
+    for _ in range(args.steps):
+        t, cores, its = cpu_full_solve(A, b, args.p)
+        secs.append(t)
+    total = sum(secs)
+    value = args.steps / total
+    sample = (f"{args.steps} full oracle solves (n={args.n}, p={args.p}, {its} iterations each, "
+              f"{statistics.mean(secs):.1f} s each on {cores} threads)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": args.n, "p": args.p, "tol": TOL,
-                       "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": info[0],
-                             "kind": "oracle", "sample": info[1]},
+            "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": run_config(args.n, args.p, args.product),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def detail(name, obj):
+    """One additional measurement on its own output line."""
+    print(json.dumps({"detail": name, **obj}), flush=True)
 
 
 def main():
@@ -516,7 +601,8 @@ def main():
     db = torch.from_numpy(b).to(dev)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    solver = ccg.Solver(device=local, stream=stream.cuda_stream)
+    prec = ccg.FP64_SLICED if args.product == "sliced" else ccg.FP64
+    solver = ccg.Solver(device=local, stream=stream.cuda_stream, precision=prec)
     maxit = args.maxit if args.maxit > 0 else 20 * n
 
     if args.profile == "mixed":
@@ -602,14 +688,6 @@ def main():
     kernel_ms = [r.device_ms for r in results]
     r0 = results[-1]
 
-    # A.D block product alone (same device code as each iteration's A-pass)
-    V = torch.randn(n, p, dtype=torch.float64, device=dev)
-    W = torch.empty(n, p, dtype=torch.float64, device=dev)
-    for _ in range(3):
-        solver.block_product(dA, V, W, want_grams=True)
-    bp = [solver.block_product(dA, V, W, want_grams=True)[3] for _ in range(10)]
-    bp_ms = statistics.mean(bp)
-
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -633,29 +711,69 @@ def main():
                "h2d_bytes_per_step": int(A.nbytes + b.nbytes),
                "d2h_bytes_per_step": int(8 * n + 192)}
 
-    mixed = lowp = batched = serving = sweep = sweep_sliced = precision = None
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    targets = {}
     if rank == 0 and not args.no_mixed:
         from paper_1204_0069_gb300 import workloads as wl
-        peaks0 = measured_peaks()
-        sweep = p_sweep(ccg, solver, stream, dA, db, x, n)
+        fp64_tf = fp64_dgemm_tflops(dev)
+        detail("fp64_peak", {"dgemm_tflops": fp64_tf,
+                             "how": "torch.matmul FP64 8192^3 (cuBLAS DGEMM), best of 5"})
+        with ccg.Solver(stream=stream.cuda_stream) as s64:
+            sweep = p_sweep(ccg, s64, stream, dA, db, x, n)
         sweep_sliced = sliced_sweep(ccg, stream, dA, db, x, n)
+        golden = {str(q): oracle_golden_iterations(n, q) for q in (1, 4, 8, 16, 32)}
+        detail("p_sweep_n8192", {"fp64_pipe": sweep, "fp64_sliced": sweep_sliced,
+                                 "oracle_iterations_stored": golden})
+        qs = (1, 4, 8, 16, 32)
+        targets["p_sweep_n8192"] = {
+            "p": list(qs),
+            "it_oracle_stored": [golden[str(q)] for q in qs],
+            "it_pipe": [sweep[str(q)]["iterations"] for q in qs],
+            "it_sliced": [sweep_sliced[str(q)]["iterations"] if str(q) in sweep_sliced else None
+                          for q in qs],
+            "ms_pipe": [round(sweep[str(q)]["ms"], 1) for q in qs],
+            "ms_sliced": [round(sweep_sliced[str(q)]["ms"], 1) if str(q) in sweep_sliced
+                          else None for q in qs]}
         A3 = device_exp_kernel(args.lowp_n, 2, 0.1, 1e-3, dev)
-        lowp = lowp_roofline(ccg, solver, dev, A3, 16, peaks0.get("hbm_gbs"))
+        lowp = lowp_roofline(ccg, solver, dev, A3, 16, hbm)
+        detail("apass_lowp_n32768", lowp)
+        targets["apass_frac_of_measured_hbm_n32768_p16"] = {
+            k.split("_")[0] if k != "fp64_sliced" else "sliced":
+            round(v["frac_of_measured_hbm"], 3) if v["frac_of_measured_hbm"] else None
+            for k, v in lowp.items()}
         precision = precision_lines(ccg, stream, A3, p=16)
+        detail("precision_n32768", precision)
         del A3
         torch.cuda.empty_cache()
+        def prow(v):
+            sp = [round(v[k], 2) if v.get(k) else None
+                  for k in ("speedup_vs_fp64_pipe", "speedup_vs_fp64_sliced")]
+            return [round(v["solves_per_s"], 3), v["status"].replace("CCG_", ""),
+                    float("%.1e" % v["relres_true"]),
+                    float("%.1e" % v["err_vs_fp64"]) if "err_vs_fp64" in v else None] + sp
+        targets["precision_n32768_p16"] = {
+            "cols": ["solves/s", "status", "relres", "err_vs_fp64", "x_vs_pipe", "x_vs_sliced"],
+            **{k: prow(precision[k]) for k, _, _, _ in PRECISION_METHODS}}
         mixed = {"exp_kernel_n8192": mixed_lines(ccg, dev, stream, A, b, p, 2)}
         Ag, bg = wl.gram_shift(n, seed=3, shift=0.5)
         mixed["gram_shift_n8192"] = mixed_lines(ccg, dev, stream, Ag, bg, p, 3)
-        mixed["gram_shift_n8192"]["workload"] = ("A = G G^T / n + 0.5 I, G ~ N(0,1), n = 8192 "
-                                                 "(batching family, seed 3), p = 8")
+        detail("mixed_n8192", mixed)
         batched = batched_line(ccg, dev, stream)
+        detail("batched", batched)
+        targets["batched_4096"] = {"fp64_solves_per_s": round(batched["fp64"]["solves_per_s"]),
+                                   "fp32_ir_solves_per_s": round(batched["fp32_ir"]["solves_per_s"]),
+                                   "all_ok": batched["fp64"]["all_ok"] and batched["fp32_ir"]["all_ok"]}
         serving = {"workload": ("Poisson(2000/s) arrivals, A from a pool of 16 device-resident "
                                 "exponential-kernel matrices, n log-uniform [256, 16384], "
-                                "tol {1e-6, 1e-10}, p = 8, 8 workers, budget 150 GB"),
-                   "fp64": serving_line(ccg, dev, ccg.FP64),
-                   "fp64_sliced": serving_line(ccg, dev, ccg.FP64_SLICED),
-                   "fp32_ir": serving_line(ccg, dev, ccg.FP32_IR)}
+                                "tol {1e-6, 1e-10}, p = 8, 8 workers, budget 150 GB")}
+        for name, pr in (("fp64_sliced", ccg.FP64_SLICED), ("fp32", ccg.FP32_IR),
+                         ("bf16", ccg.BF16_IR), ("fp64_pipe", ccg.FP64)):
+            serving[name] = serving_line(ccg, dev, pr)
+        detail("serving", serving)
+        targets["serving_p50_p99_ms"] = {k: [round(v["p50_ms"]), round(v["p99_ms"])]
+                                         for k, v in serving.items() if isinstance(v, dict)}
+        targets["fp64_dgemm_tflops"] = round(fp64_tf, 3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -665,58 +783,45 @@ def main():
 
     if rank == 0:
         checks = 1 + r0.replacements
-        fl = solve_flops(n, p, r0.iterations, checks, r0.replacements)
-        by = solve_bytes(n, p, r0.iterations, checks, r0.replacements)
         kms = statistics.mean(kernel_ms)
-        peaks = measured_peaks()
-        fp64_peak = 1.25  # TFLOP/s: nominal GB300 FP64 rate (no measured FP64 figure)
-        achieved = fl / (kms / 1e3) / 1e12
-        per_pass = NCU_BYTES_PER_PASS.get((n, p))
-        traffic = (per_pass * (1 + r0.iterations + checks + r0.replacements)
-                   if per_pass is not None else None)
+        passes = 1 + r0.iterations + r0.replacements
+        if args.product == "sliced":
+            # the sliced A (14 n^2 bytes) per block product, the FP64 A per check
+            byts = 14.0 * n * n * passes + 8.0 * n * n * checks + 80.0 * n * p * r0.iterations
+            achieved = byts / (kms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm if hbm else None,
+                    "traffic": None,
+                    "kernel": f"fp64_kernel<{p_bucket(p)},true,POL_SLICED>",
+                    "note": "14n^2 B per block product, 8n^2 per FP64 check; peak measured"}
+        else:
+            fl = solve_flops(n, p, r0.iterations, checks, r0.replacements)
+            achieved = fl / (kms / 1e3) / 1e12
+            fp64_peak = 1.25
+            per_pass = NCU_BYTES_PER_PASS.get(("fp64", n, p))
+            roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak,
+                    "traffic": per_pass * (passes + checks) if per_pass else None,
+                    "kernel": f"fp64_kernel<{p_bucket(p)},true>",
+                    "note": "nominal FP64 peak (targets.fp64_dgemm_tflops: measured)"}
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "p": p, "tol": TOL,
-                       "l2": "inputs larger than L2 (A = 512 MiB FP64 > 129 MB)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": run_config(n, p, args.product),
             "iterations": r0.iterations, "relres_true": r0.relres_true,
-            "latency_ms": {"p50": float(np.percentile(kernel_ms, 50)),
-                           "p99": float(np.percentile(kernel_ms, 99))},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
-                         "traffic_note": ("DRAM bytes per launch, scaled from an ncu capture "
-                                          "of a 20-iteration solve (bytes per pass x passes)"),
-                         "kernel": f"fp64_kernel<{p_bucket(p)},true> (persistent solve)",
-                         "peak_note": "nominal FP64 rate (FP64 pipe bound)"},
-            "apass": {"ms": bp_ms, "gbs": 8.0 * n * n / (bp_ms / 1e3) / 1e9,
-                      "tflops": 2.0 * n * n * p / (bp_ms / 1e3) / 1e12,
-                      "hbm_peak_gbs": peaks.get("hbm_gbs")},
-            "algorithmic": {"flops_per_solve": fl, "bytes_per_solve": by},
-            "gpu_launches": args.steps,
-            "clocks": clk,
+            "roofline": roof, "clocks": clk,
+            # per step: the slicing of A and the persistent solve (sliced), or the solve
+            "gpu_launches": (2 if args.product == "sliced" else 1) * args.steps,
         }
-        if sweep is not None:
-            line["p_sweep"] = sweep
-        if sweep_sliced is not None:
-            line["p_sweep_fp64_sliced"] = sweep_sliced
-        if lowp is not None:
-            line["lowp_apass"] = lowp
-        if precision is not None:
-            line["precision"] = precision
-        if mixed is not None:
-            line["mixed"] = mixed
-        if batched is not None:
-            line["batched"] = batched
-        if serving is not None:
-            line["serving"] = serving
         if e2e is not None:
             line["e2e"] = e2e
         if cpu is not None:
             line["cpu_baseline"] = cpu
-        print(json.dumps(line), flush=True)
+        if targets:
+            line["targets"] = targets
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     solver.close()
     if dist is not None:
         dist.destroy_process_group()

@@ -138,11 +138,12 @@ extern "C" int ccg_solve_noalloc(int device, void* stream, int64_t n, const doub
   prm.expected_ctas = (unsigned)G;
 
   // Solver state: zeroed, then the fields that do not start at zero.  The
-  // leading part of the state (counters, agent map) is staged on the stack.
+  // leading part of the state (counters, agent map) is staged through a
+  // state object on the stack (about 60 KB; no heap memory).
   constexpr size_t kHead = offsetof(ccg::DevState, s);
-  unsigned char head[kHead];
-  std::memset(head, 0, sizeof(head));
-  ccg::DevState* hs = reinterpret_cast<ccg::DevState*>(head);
+  ccg::DevState hstate;
+  std::memset(&hstate, 0, sizeof(hstate));
+  ccg::DevState* hs = &hstate;
   hs->pk = p;
   hs->prev_pk = p;
   hs->k_replaced = -1;
@@ -150,9 +151,9 @@ extern "C" int ccg_solve_noalloc(int device, void* stream, int64_t n, const doub
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(prm.st, 0, sizeof(ccg::DevState), s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(prm.st, head, kHead, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(prm.st, hs, kHead, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = ccg::launch_fp64(prm, P, vec, G, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(head, prm.st, kHead, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs, prm.st, kHead, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -1524,10 +1524,11 @@ __device__ __forceinline__ void lp_put(const Params& prm, int j, int64_t i, doub
 // preconv: the operand rows already hold V in the MMA type (written by the
 // D-update, followed by a grid barrier), so the conversion and its barrier
 // are skipped.
-template <int P, int POL>
-__device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, bool sub_b,
-                         int64_t r0, int64_t r1, LpCtx& L, SyncShared* ss, int* s_err,
-                         bool preconv = false) {
+// The fixup hands each finished entry (row i, column j, value of A_lp V with
+// the scales applied) to `epi`; lp_apass below stores it (minus b) in Y.
+template <int P, int POL, class Epi>
+__device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t r0, int64_t r1,
+                             LpCtx& L, SyncShared* ss, int* s_err, bool preconv, Epi epi) {
   constexpr int KIND = LpCfg<POL>::KIND;
   constexpr int NP = LpNP<P, POL>::value;
   DevState* st = prm.st;
@@ -1651,8 +1652,7 @@ __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, 
           s += __ldcg(part + ((size_t)(cc + tr) * tc::kBM + rr) * NP + j);
         }
         s *= (double)prm.lp_row_scale[i] * (double)__ldcg(&st->sigma[j]);
-        if (sub_b) s -= prm.b[i];
-        Y[i * p + j] = s;
+        epi(i, j, s);
       }
       __syncthreads();
     }
@@ -1674,12 +1674,23 @@ __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, 
     }
     if (prm.lp_row_scale) s *= (double)prm.lp_row_scale[i];
     if constexpr (KIND == tc::KIND_FP8) s *= (double)__ldcg(&st->sigma[j]);
-    if (sub_b) s -= prm.b[i];
-    Y[i * p + j] = s;
+    epi(i, j, s);
   }
   __syncthreads();
   return true;
   }
+}
+
+template <int P, int POL>
+__device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, bool sub_b,
+                         int64_t r0, int64_t r1, LpCtx& L, SyncShared* ss, int* s_err,
+                         bool preconv = false) {
+  const int p = prm.p;
+  return lp_apass_epi<P, POL>(prm, V, pk, r0, r1, L, ss, s_err, preconv,
+                              [&](int64_t i, int j, double v) {
+                                if (sub_b) v -= prm.b[i];
+                                Y[i * p + j] = v;
+                              });
 }
 
 // --------------------------------------------------------------------------
@@ -1869,22 +1880,33 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
             sr[o] = r;
           }
           __syncthreads();
+          // each step: W = A_lp d ; S -= W ; d = c1 d + c2 S ; Z += d, the update
+          // done on the fixup's entries as they are summed; BF16 / TF32 also
+          // write the next step's operand rows there (no separate conversion)
+          constexpr bool kConvInFixup = POL == POL_BF16 || POL == POL_TF32X3;
+          bool conv = false;
           for (int k = 1; k < prm.cheb_steps; ++k) {
-            // W = A_lp d ; S -= W ; d = c1 d + c2 S ; Z += d
-            if (!lp_apass<P, POL>(prm, d, pk, prm.cheb_w, false, r0, r1, *L, &ss, &s_err))
-              return;
             const double rn = 1.0 / (2.0 * sg - rho);
             const double c1 = rn * rho, c2 = 2.0 * rn / de;
-            for (int64_t idx = tid; idx < cnt; idx += kThreads) {
-              const int64_t o = (r0 + idx / pk) * p + idx % pk;
-              const double sv = sr[o] - ldcg(prm.cheb_w + o);
-              const double dv = c1 * d[o] + c2 * sv;
-              sr[o] = sv;
-              d[o] = dv;
-              Z[o] += dv;
-            }
+            const bool conv_next = kConvInFixup && k + 1 < prm.cheb_steps;
+            const bool ok = lp_apass_epi<P, POL>(
+                prm, d, pk, r0, r1, *L, &ss, &s_err, conv, [&](int64_t i, int j, double w) {
+                  const int64_t o = i * p + j;
+                  const double sv = sr[o] - w;
+                  const double dv = c1 * d[o] + c2 * sv;
+                  sr[o] = sv;
+                  d[o] = dv;
+                  Z[o] += dv;
+                  if (conv_next) lp_put<LpCfg<POL>::KIND, LpNP<P, POL>::value>(prm, j, i, dv);
+                });
+            if (!ok) return;
             rho = rn;
-            __syncthreads();
+            if (conv_next) {
+              // the operand rows of every CTA are complete before the next pass
+              asm volatile("fence.proxy.async.global;" ::: "memory");
+              if (!grid_barrier(prm, &ss, &s_err)) return;
+            }
+            conv = conv_next;
           }
           return;
         }

@@ -4,9 +4,14 @@ orthogonal, L uniform in [1, kappa], b and the agents' starts uniform in
 tol = 1e-3 / ||b|| relative).  The paper reports that cCG with p = 3 needs
 fewer iterations than CG on every size it tried (Fig. 2, Table 4; average
 iteration speed-up 1.62).  On seeded instances of the family the GPU solver
-must show the same direction, and each solve must meet its tolerance."""
+must show the same direction, each solve must meet its tolerance, and each
+must match the FP64 oracle run from the same agents' starts: iteration count
+within the oracle's rounding envelope (tests/envelope.py; kappa = 1e6) and
+||x - x_oracle|| / ||x_oracle|| <= 100 tol (the FP64 bar, 1e-8 at tol 1e-10,
+scaled to the paper's looser tolerance)."""
 import numpy as np
 import pytest
+from envelope import oracle_counts, within_envelope
 
 from paper_1204_0069_gb300 import workloads as wl
 
@@ -21,7 +26,9 @@ def env():
     from paper_1204_0069_gb300 import build as B
     B.build()
     from paper_1204_0069_gb300 import ccg
-    return dict(torch=torch, ccg=ccg)
+    import oracle
+    oracle.build()
+    return dict(torch=torch, ccg=ccg, oracle=oracle)
 
 
 @pytest.mark.parametrize("n,seed", [(1000, 5), (1500, 6)])
@@ -41,4 +48,9 @@ def test_cooperation_reduces_iterations_on_paper_family(env, n, seed):
             xs = x.cpu().numpy()
             assert np.linalg.norm(b - A @ xs) <= 1e-3 * 1.001
             its[p] = r.iterations
+            ref, counts, status = oracle_counts(env["oracle"], A, b, X0[:, :p], tol, 50 * n)
+            assert all(st == 0 for st in status), status
+            assert within_envelope(r.iterations, counts), (p, r.iterations, counts)
+            err = np.linalg.norm(xs - ref["x"]) / np.linalg.norm(ref["x"])
+            assert err <= 100.0 * tol, (p, err)
     assert its[3] < its[1], its

@@ -7,7 +7,8 @@ fixed device array.  This file runs last (its name sorts last) so that a run
 stopping at the first failure has already run every other test; it also
 passes on its own in a fresh process.  Same tolerances as the parity tests:
 ||x - x_ref|| / ||x_ref|| <= 1e-8 and iterations within 2, on two calls in a
-row (the second call reuses the scratch the first one left behind).
+row (the second call reuses the scratch the first one left behind), and the
+second call leaves the device's free memory where it found it.
 """
 import numpy as np
 import pytest
@@ -46,9 +47,16 @@ def test_noalloc_matches_solve_on_two_calls(env, case):
     assert r_ref.status == 0
     xr = x_ref.cpu().numpy()
     stream = torch.cuda.current_stream().cuda_stream
-    for _ in range(2):
+    for call in range(2):
         x = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         r = ccg.solve_noalloc(dA, db, x, p=p, tol=1e-10, maxit=10 * n, device=0, stream=stream)
+        free1 = torch.cuda.mem_get_info()[0]
+        if call == 1:
+            # the first call loaded the module and looked up the scratch array;
+            # the second one takes no device memory at all
+            assert free1 >= free0, (free0, free1)
         assert r.status == 0, r
         assert r.relres_true <= 1e-10
         xg = x.cpu().numpy()
