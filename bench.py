@@ -47,8 +47,10 @@ GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on
 # 20-iteration solves of the benchmark system (22 passes; the traffic grows
 # with the passes, so a full solve is scaled from it).  FP64 pipe, p = 8:
-# 11 853.2 MB; sliced product: see profiles/sliced_fp64_solve_traffic_n8192.md.
-NCU_BYTES_PER_PASS = {("fp64", 8192, 8): (11814291712 + 45762304) / 22.0}
+# 11 853.2 MB; sliced product (21 sliced passes and one FP64 check over the
+# FP64 A): 946.8 MB per sliced pass, profiles/sliced_fp64_solve_traffic_n8192_p8.md.
+NCU_BYTES_PER_PASS = {("fp64", 8192, 8): (11814291712 + 45762304) / 22.0,
+                      ("sliced", 8192, 8): (20316387840 + 104307200 - 8.0 * 8192 ** 2) / 21.0}
 
 
 def run_config(n, p, product):
@@ -789,9 +791,10 @@ def main():
             # the sliced A (14 n^2 bytes) per block product, the FP64 A per check
             byts = 14.0 * n * n * passes + 8.0 * n * n * checks + 80.0 * n * p * r0.iterations
             achieved = byts / (kms / 1e3) / 1e9
+            per_pass = NCU_BYTES_PER_PASS.get(("sliced", n, p))
             roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm if hbm else None,
-                    "traffic": None,
+                    "traffic": (per_pass * passes + 8.0 * n * n * checks) if per_pass else None,
                     "kernel": f"fp64_kernel<{p_bucket(p)},true,POL_SLICED>",
                     "note": "14n^2 B per block product, 8n^2 per FP64 check; peak measured"}
         else:

@@ -111,7 +111,7 @@ typedef struct {
     double cheb_ratio;          /* CCG_MIXED_PRECOND: lower end of the
                                    Chebyshev interval as a fraction of the
                                    upper end (a bound on the largest
-                                   eigenvalue); 0 = 3e-4                      */
+                                   eigenvalue); 0 = 1e-4                      */
 } ccg_config;
 
 /* Mixed-precision methods (ccg_config.mixed_method).
@@ -364,6 +364,14 @@ typedef struct {
     int precision;          /* ccg_precision of every solve; CCG_FP64            */
     double budget_bytes;    /* device bytes the admitted requests may hold; 150e9 */
     int ctas_per_worker;    /* SM share of one solve; 0 = SMs / workers          */
+    int slots;              /* 0 (default): worker threads as above.  > 0: one
+                               persistent serving kernel with `slots` slots of
+                               SMs / slots CTAs each (continuous batching, see
+                               ccg_server_create); CCG_FP64 only             */
+    int64_t max_n;          /* slots mode: largest n accepted; the slots' X, R,
+                               D and A D blocks are allocated for it at
+                               creation; 0 = 16384                          */
+    int max_p;              /* slots mode: largest p accepted (8 or 32); 0 = 8 */
 } ccg_server_config;
 
 typedef struct {
@@ -371,7 +379,7 @@ typedef struct {
     int status;             /* ccg_status of the solve                          */
     int iterations;
     int outer_steps;        /* mixed precision: refinement steps               */
-    int worker;
+    int worker;             /* worker, or slot in slots mode                    */
     int ctas;
     double relres_true;     /* ||b - A x|| / ||b|| in FP64                       */
     double submit_ms;       /* server clock (ms since ccg_server_create)        */
@@ -389,14 +397,30 @@ typedef struct {
 void ccg_server_config_init(ccg_server_config* cfg);
 
 /*
- * Start a server: `workers` threads, each with its own handle and stream and
- * a fixed share of the SMs.  Requests are admitted in arrival order, first
- * fit: a free worker takes the oldest queued request whose device memory
- * (its matrix, kept resident for the request's lifetime, plus workspace and,
- * for mixed precision, the quantised copy) fits in the budget left by the
- * running requests.  Requests admitted while others run execute concurrently
- * on the device.  A request's grid depends only on its size and the worker
- * share, so its result does not depend on what else is running.
+ * Start a server.
+ *
+ * Worker mode (slots = 0): `workers` threads, each with its own handle and
+ * stream and a fixed share of the SMs.  Requests are admitted in arrival
+ * order, first fit: a free worker takes the oldest queued request whose
+ * device memory (its matrix, kept resident for the request's lifetime, plus
+ * workspace and, for mixed precision, the quantised copy) fits in the budget
+ * left by the running requests.  Requests admitted while others run execute
+ * concurrently on the device.
+ *
+ * Slots mode (slots > 0, CCG_FP64): one persistent kernel serves every
+ * request.  Its grid is split into `slots` slots of SMs / slots CTAs; each
+ * slot keeps its cCG state and its X, R, D, A D blocks resident (allocated
+ * once, for max_n and max_p) and takes the next admitted request from a ring
+ * in host memory that the server appends to while the kernel runs, so a
+ * request starts as soon as a slot is free and the work of all slots runs in
+ * the same launch (continuous batching; no allocation and no launch per
+ * request).  Admission is first fit in arrival order under the budget (the
+ * request's matrix).  The kernel ends after a short idle time and is
+ * launched again when requests arrive.  A must be 16-byte aligned with an
+ * even lda, n <= max_n, p <= max_p.
+ *
+ * In both modes a request's grid depends only on its size and the share (or
+ * slot), so its result does not depend on what else is running.
  */
 int ccg_server_create(const ccg_server_config* cfg, ccg_server** out);
 

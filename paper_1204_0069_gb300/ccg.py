@@ -45,7 +45,8 @@ class Config(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("workers", ctypes.c_int), ("precision", ctypes.c_int),
-                ("budget_bytes", ctypes.c_double), ("ctas_per_worker", ctypes.c_int)]
+                ("budget_bytes", ctypes.c_double), ("ctas_per_worker", ctypes.c_int),
+                ("slots", ctypes.c_int), ("max_n", ctypes.c_int64), ("max_p", ctypes.c_int)]
 
 
 class ServerResult(ctypes.Structure):
@@ -350,15 +351,25 @@ class LowpMatrix:
 
 
 class Server:
-    """A serving loop (ccg_server_create): submit requests, poll results."""
+    """A serving loop (ccg_server_create): submit requests, poll results.
+    Worker threads by default; slots > 0 serves every request from one
+    persistent kernel (continuous batching)."""
 
     def __init__(self, device: int = 0, workers: int = 8, precision: int = 0,
-                 budget_bytes: float = 150e9, ctas_per_worker: int = 0):
+                 budget_bytes: float = 150e9, ctas_per_worker: int = 0, slots: int = 0,
+                 max_n: int = 0, max_p: int = 0):
+        """slots > 0: one persistent serving kernel with that many slots
+        (continuous batching, CCG_FP64); otherwise `workers` worker threads."""
         L = lib()
         c = ServerConfig()
         L.ccg_server_config_init(ctypes.byref(c))
         c.device, c.workers, c.precision = device, workers, precision
         c.budget_bytes, c.ctas_per_worker = budget_bytes, ctas_per_worker
+        c.slots = slots
+        if max_n:
+            c.max_n = max_n
+        if max_p:
+            c.max_p = max_p
         h = _VP()
         rc = L.ccg_server_create(ctypes.byref(c), ctypes.byref(h))
         if rc != 0:

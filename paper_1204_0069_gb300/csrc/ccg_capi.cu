@@ -291,7 +291,7 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
     cp.lp_ldk = ldk0;
     cp.lp_part = ppart;
     cp.cheb_steps = h->cfg.cheb_degree > 0 ? h->cfg.cheb_degree : 32;
-    const double ratio = h->cfg.cheb_ratio > 0.0 ? h->cfg.cheb_ratio : 3e-4;
+    const double ratio = h->cfg.cheb_ratio > 0.0 ? h->cfg.cheb_ratio : 1e-4;
     prm.precond = 1;
     prm.Z = cp.Z;
     if (!ccg::lp::make_tensor_map(&cp.lp_tmA, pre->q, pre_kd, n, n, pre->ldq, 128) ||

@@ -106,6 +106,44 @@ struct DevState {
   double red[kPartHalf];    // cross-CTA sums of the partial slots (same offsets)
 };
 
+// Serving kernel: one request of the ring (written by the host).
+struct ServeDesc {
+  int64_t n, lda;
+  const double* A;
+  const double* b;
+  double* x;
+  double tol;
+  int maxit;
+  int p;
+  int64_t seq;             // ring position + 1 once written (guards against stale reads)
+};
+// Claim and result of one ring entry (written by the kernel, read by the host).
+struct ServeOut {
+  int64_t claimed;         // seq once a slot took the request
+  int64_t done;            // seq once the result below is final
+  int status;
+  int iterations;
+  double relres_true;
+  int slot;
+  int pad;
+  long long t_start_ns;    // device clock (%globaltimer) at claim and at the end
+  long long t_end_ns;
+};
+// Per slot: arrival counter and generation of the slot barrier, the ticket
+// (ring position of the slot's next request, or -1: leave).
+struct SlotSync {
+  unsigned count;
+  unsigned gen;
+  int ticket;
+  int pad;
+};
+struct ServeCtl {
+  unsigned head;           // requests claimed
+  int busy;                // slots working on a request
+  int closing;             // 1: every slot leaves once idle
+  int error;               // a slot barrier gave up (CCG_ERR_TIMEOUT)
+};
+
 struct Params {
   int64_t n;
   int64_t lda;
@@ -196,6 +234,18 @@ struct Params {
   int cheb_steps;          // products with A_lp per application
   double cheb_lo;          // interval [cheb_lo, cheb_hi] of the Chebyshev polynomial
   double cheb_hi;
+  // serving kernel (continuous batching): slots of serve_group CTAs, each
+  // taking requests from a queue the host appends to while the kernel runs
+  int serve_group;               // CTAs per slot
+  int serve_capacity;            // request ring entries
+  const ServeDesc* serve_desc;   // request ring (host memory mapped into the device)
+  const int* serve_tail;         // requests posted (host writes, mapped)
+  const int* serve_stop;         // 1: leave once idle (host writes, mapped)
+  ServeOut* serve_out;           // per ring entry: claim and result (mapped)
+  SlotSync* serve_sync;          // per slot: barrier words and ticket (device)
+  ServeCtl* serve_ctl;           // claim counter, busy slots, closing flag (device)
+  int64_t serve_ws_stride;       // doubles of X, R, D0, D1, W per slot
+  long long serve_idle_ns;       // leave after this long with nothing to do
   CUtensorMap lp_tmA;  // A_lp tiles (the type carries its alignment)
   CUtensorMap lp_tmB;  // operand tiles
 };
@@ -213,5 +263,8 @@ cudaError_t launch_fp64(const Params& prm, int P, bool vec, int ctas,
 // ir: the FP32-refinement variant (batch_ir_kernel).
 int batch_ctas_per_sm(int P, bool ir = false);
 cudaError_t launch_batch(const Params& prm, int P, int ctas, cudaStream_t stream, bool ir = false);
+// Serving kernel (slots of CTAs over a request ring): occupancy and launch.
+int serve_ctas_per_sm(int P);
+cudaError_t launch_serve(const Params& prm, int P, int ctas, cudaStream_t stream);
 
 }  // namespace ccg

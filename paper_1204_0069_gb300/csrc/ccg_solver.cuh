@@ -36,6 +36,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include <cuda_bf16.h>
@@ -1588,22 +1589,32 @@ __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t
     asm volatile("fence.proxy.async.global;" ::: "memory");
     if (!grid_barrier(prm, ss, s_err)) return false;
   } else if (!preconv) {
-    // operand row j (< NP) holds column j of V, zero beyond pk
-    for (int64_t idx = tid; idx < (int64_t)NP * nr; idx += kThreads) {
-      const int j = (int)(idx / nr);
-      const int64_t i = r0 + (idx - (int64_t)j * nr);
-      const double v = (j < pk) ? ldcg(V + i * p + j) : 0.0;
-      if constexpr (KIND == tc::KIND_FP8) {
-        const float sg = (j < pk) ? __ldcg(&st->sigma[j]) : 1.f;
-        const double x = v / (double)sg;
-        const __nv_fp8_storage_t h = __nv_cvt_double_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
-        const double hv = (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(h, __NV_E4M3)));
-        const __nv_fp8_storage_t l = __nv_cvt_double_to_fp8(x - hv, __NV_SATFINITE, __NV_E4M3);
-        uint8_t* o = reinterpret_cast<uint8_t*>(prm.lp_dq);
-        o[(int64_t)j * ldk + i] = (uint8_t)h;
-        o[(int64_t)(NP + j) * ldk + i] = (uint8_t)l;
-      } else {
-        lp_put<KIND, NP>(prm, j, i, v);
+    // operand row j (< NP) holds column j of V, zero beyond pk; a thread
+    // takes whole rows of V (contiguous reads), the byte rows are written
+    // across consecutive threads
+    __shared__ double s_inv[32];  // FP8: 1 / sigma_j
+    if constexpr (KIND == tc::KIND_FP8) {
+      for (int j = tid; j < NP; j += kThreads)
+        s_inv[j] = j < pk ? 1.0 / (double)__ldcg(&st->sigma[j]) : 0.0;
+      __syncthreads();
+    }
+    for (int li = tid; li < (int)nr; li += kThreads) {
+      const int64_t i = r0 + li;
+      const double* vr = V + i * p;
+#pragma unroll 4
+      for (int j = 0; j < NP; ++j) {
+        const double v = (j < pk) ? ldcg(vr + j) : 0.0;
+        if constexpr (KIND == tc::KIND_FP8) {
+          const double x = v * s_inv[j];
+          const __nv_fp8_storage_t h = __nv_cvt_double_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+          const double hv = (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(h, __NV_E4M3)));
+          const __nv_fp8_storage_t l = __nv_cvt_double_to_fp8(x - hv, __NV_SATFINITE, __NV_E4M3);
+          uint8_t* o = reinterpret_cast<uint8_t*>(prm.lp_dq);
+          o[(int64_t)j * ldk + i] = (uint8_t)h;
+          o[(int64_t)(NP + j) * ldk + i] = (uint8_t)l;
+        } else {
+          lp_put<KIND, NP>(prm, j, i, v);
+        }
       }
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -1612,73 +1623,82 @@ __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t
   lp_pass<KIND, NP>(prm, L);
   if (!grid_barrier(prm, ss, s_err)) return false;
   // fixup: each owned row sums the partial tiles of the CTAs that covered it
+  // (FP32 tiles; FP64 with the slices already summed for the sliced kind),
+  // in CTA order.  The CTA range of each row tile of this CTA's rows is found
+  // once, kRng row tiles at a time; a thread then takes a whole row and
+  // reads its partial rows four columns at a time.
   const int G = gridDim.x;
   const int64_t U = prm.lp_units;
   const int kc = prm.lp_kc;
-  if constexpr (KIND == tc::KIND_SLICED) {
-    // FP64 partial tiles, one per (row tile, CTA) with the slices already
-    // summed; the CTA ranges of the row tiles of this CTA's rows are found
-    // once, kRng row tiles at a time
-    constexpr int kRng = 8;
-    __shared__ int s_rng[kRng][2];
-    const int tr0 = (int)(r0 / tc::kBM);
-    const int ntr = (nr > 0) ? (int)((r1 - 1) / tc::kBM) - tr0 + 1 : 0;
-    const double* part = reinterpret_cast<const double*>(prm.lp_part);
-    const bool some_empty = U < G;  // with U >= G every CTA holds a unit
-    for (int q0 = 0; q0 < ntr; q0 += kRng) {
-      const int nq = min(kRng, ntr - q0);
-      for (int q = tid; q < nq; q += kThreads) {
-        const int64_t lo = (int64_t)(tr0 + q0 + q) * tc::kSlices * kc;
-        const int64_t hi = lo + (int64_t)tc::kSlices * kc;
-        int c0 = (int)((lo * G) / U);
-        while (c0 > 0 && tc::unit_begin(U, G, c0) > lo) --c0;
-        while (tc::unit_begin(U, G, c0 + 1) <= lo) ++c0;
-        int c1 = c0;
-        while (c1 + 1 < G && tc::unit_begin(U, G, c1 + 1) < hi) ++c1;
-        s_rng[q][0] = c0;
-        s_rng[q][1] = c1;
-      }
-      __syncthreads();
-      const int64_t ra = max(r0, (int64_t)(tr0 + q0) * tc::kBM);
-      const int64_t rb = min(r1, (int64_t)(tr0 + q0 + nq) * tc::kBM);
-      for (int64_t idx = tid; idx < (rb - ra) * pk; idx += kThreads) {
-        const int64_t i = ra + idx / pk;
-        const int j = (int)(idx - (idx / pk) * pk);
-        const int tr = (int)(i / tc::kBM);
-        const int rr = (int)(i - (int64_t)tr * tc::kBM);
-        double s = 0.0;
-        for (int cc = s_rng[tr - tr0 - q0][0]; cc <= s_rng[tr - tr0 - q0][1]; ++cc) {
+  using PartT = typename std::conditional<KIND == tc::KIND_SLICED, double, float>::type;
+  const PartT* part = reinterpret_cast<const PartT*>(prm.lp_part);
+  const int64_t per_tile = (KIND == tc::KIND_SLICED) ? (int64_t)tc::kSlices * kc : (int64_t)kc;
+  constexpr int kRng = 8;
+  __shared__ int s_rng[kRng][2];
+  const int tr0 = (int)(r0 / tc::kBM);
+  const int ntr = (nr > 0) ? (int)((r1 - 1) / tc::kBM) - tr0 + 1 : 0;
+  const bool some_empty = U < G;  // with U >= G every CTA holds a unit
+  for (int q0 = 0; q0 < ntr; q0 += kRng) {
+    const int nq = min(kRng, ntr - q0);
+    for (int q = tid; q < nq; q += kThreads) {
+      const int64_t lo = (int64_t)(tr0 + q0 + q) * per_tile;
+      const int64_t hi = lo + per_tile;
+      int c0 = (int)((lo * G) / U);
+      while (c0 > 0 && tc::unit_begin(U, G, c0) > lo) --c0;
+      while (tc::unit_begin(U, G, c0 + 1) <= lo) ++c0;
+      int c1 = c0;
+      while (c1 + 1 < G && tc::unit_begin(U, G, c1 + 1) < hi) ++c1;
+      s_rng[q][0] = c0;
+      s_rng[q][1] = c1;
+    }
+    __syncthreads();
+    const int64_t ra = max(r0, (int64_t)(tr0 + q0) * tc::kBM);
+    const int nrow = (int)(min(r1, (int64_t)(tr0 + q0 + nq) * tc::kBM) - ra);
+    for (int li = tid; li < nrow; li += kThreads) {
+      const int64_t i = ra + li;
+      const int tr = (int)(i / tc::kBM);
+      const int rr = (int)(i - (int64_t)tr * tc::kBM);
+      const int c0 = s_rng[tr - tr0 - q0][0], c1 = s_rng[tr - tr0 - q0][1];
+      const double rs = prm.lp_row_scale ? (double)prm.lp_row_scale[i] : 1.0;
+      for (int j0 = 0; j0 < pk; j0 += 4) {
+        double sv[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int cc = c0; cc <= c1; ++cc) {
           if (some_empty && tc::unit_begin(U, G, cc + 1) <= tc::unit_begin(U, G, cc)) continue;
-          s += __ldcg(part + ((size_t)(cc + tr) * tc::kBM + rr) * NP + j);
+          const PartT* pr = part + ((size_t)(cc + tr) * tc::kBM + rr) * NP + j0;
+          if constexpr (NP >= 4) {
+            if constexpr (KIND == tc::KIND_SLICED) {
+              const double2 a = __ldcg(reinterpret_cast<const double2*>(pr));
+              const double2 b = __ldcg(reinterpret_cast<const double2*>(pr) + 1);
+              sv[0] += a.x; sv[1] += a.y; sv[2] += b.x; sv[3] += b.y;
+            } else {
+              const float4 a = __ldcg(reinterpret_cast<const float4*>(pr));
+              sv[0] += (double)a.x; sv[1] += (double)a.y;
+              sv[2] += (double)a.z; sv[3] += (double)a.w;
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (j0 + u < NP) sv[u] += (double)__ldcg(pr + u);
+          }
         }
-        s *= (double)prm.lp_row_scale[i] * (double)__ldcg(&st->sigma[j]);
-        epi(i, j, s);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          if (j >= pk) break;
+          double v = sv[u];
+          if constexpr (KIND == tc::KIND_SLICED) {
+            v *= rs * (double)__ldcg(&st->sigma[j]);
+          } else {
+            if (prm.lp_row_scale) v *= rs;
+            if constexpr (KIND == tc::KIND_FP8) v *= (double)__ldcg(&st->sigma[j]);
+          }
+          epi(i, j, v);
+        }
       }
-      __syncthreads();
     }
-    return true;
-  } else {
-  for (int64_t idx = tid; idx < nr * pk; idx += kThreads) {
-    const int64_t i = r0 + idx / pk;
-    const int j = (int)(idx - (idx / pk) * pk);
-    const int t = (int)(i / tc::kBM);
-    const int rr = (int)(i - (int64_t)t * tc::kBM);
-    const int64_t lo = (int64_t)t * kc, hi = lo + kc;
-    int c0 = (int)((lo * G) / U);
-    while (c0 > 0 && tc::unit_begin(U, G, c0) > lo) --c0;
-    while (tc::unit_begin(U, G, c0 + 1) <= lo) ++c0;
-    double s = 0.0;
-    for (int cc = c0; cc < G && tc::unit_begin(U, G, cc) < hi; ++cc) {
-      if (tc::unit_begin(U, G, cc + 1) <= tc::unit_begin(U, G, cc)) continue;
-      s += (double)__ldcg(prm.lp_part + ((size_t)(cc + t) * tc::kBM + rr) * NP + j);
-    }
-    if (prm.lp_row_scale) s *= (double)prm.lp_row_scale[i];
-    if constexpr (KIND == tc::KIND_FP8) s *= (double)__ldcg(&st->sigma[j]);
-    epi(i, j, s);
+    __syncthreads();
   }
-  __syncthreads();
   return true;
-  }
 }
 
 template <int P, int POL>
@@ -2530,6 +2550,187 @@ __global__ void __launch_bounds__(kThreads, 1) batch_ir_kernel(const __grid_cons
       prm.batch_iters[idx] = total;
       prm.batch_relres[idx] = best;
       if (prm.batch_outer) prm.batch_outer[idx] = outer;
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// Serving kernel: continuous batching of solve requests.  The grid is split
+// into slots of serve_group CTAs.  The first CTA of a slot takes the next
+// request from a ring in host memory that the host appends to while the
+// kernel runs, and hands its position to the other CTAs of the slot; the
+// slot solves it (the solver body with a group of serve_group CTAs, the
+// slot's state and workspace, A, b and x where the request points), writes
+// the result into the ring entry and takes the next request.  Requests of
+// all slots advance concurrently in this one launch; a request posted while
+// others run starts as soon as a slot frees up.  The kernel ends once the
+// host asks it to stop, or after serve_idle_ns with nothing to claim and no
+// slot busy; every wait is bounded.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire_sys_i32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ long long ld_acquire_sys_i64(const int64_t* p) {
+  long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys_i64(int64_t* p, long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Leader of a slot: the ring position of the next request, or -1 (leave).
+__device__ int serve_claim(const Params& prm) {
+  ServeCtl* ctl = prm.serve_ctl;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    if (*(volatile int*)&ctl->closing != 0 || *(volatile int*)&ctl->error != 0) return -1;
+    const unsigned h = ld_acquire_u32(&ctl->head);
+    const int t = ld_acquire_sys_i32(prm.serve_tail);
+    if ((int)h < t) {
+      if (atomicCAS(&ctl->head, h, h + 1u) == h) {
+        atomicAdd(&ctl->busy, 1);
+        return (int)h;
+      }
+      continue;
+    }
+    const bool stop = ld_acquire_sys_i32(prm.serve_stop) != 0;
+    const bool idle = globaltimer_ns() - t0 > (unsigned long long)prm.serve_idle_ns;
+    if ((stop || idle) && *(volatile int*)&ctl->busy == 0) {
+      atomicExch(&ctl->closing, 1);
+      return -1;
+    }
+    __nanosleep(500);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constant__ Params prm) {
+  extern __shared__ __align__(1024) uint8_t dyn_smem[];
+  __shared__ Params q;
+  __shared__ int s_ticket;
+  const int tid = threadIdx.x;
+  const int C = prm.serve_group;
+  const int slot = (int)blockIdx.x / C;
+  const int rank = (int)blockIdx.x - slot * C;
+  SlotSync* sy = prm.serve_sync + slot;
+  ServeCtl* ctl = prm.serve_ctl;
+  DevState* st = prm.st + slot;
+  const long long wait_ns = prm.serve_idle_ns + prm.timeout_ns;
+  unsigned gen = 0;
+  for (;;) {
+    // ---- the leader claims; the slot learns the ticket ----
+    if (tid == 0) {
+      int ticket = -1;
+      if (rank == 0) {
+        ticket = serve_claim(prm);
+        if (ticket >= 0) {
+          const ServeDesc* d = prm.serve_desc + ticket % prm.serve_capacity;
+          // the host writes the entry before it moves the tail past it
+          const unsigned long long t0 = globaltimer_ns();
+          while (ld_acquire_sys_i64(&d->seq) != (long long)ticket + 1) {
+            if (globaltimer_ns() - t0 > (unsigned long long)prm.timeout_ns) {
+              atomicExch(&ctl->error, ST_ERR_TIMEOUT);
+              atomicSub(&ctl->busy, 1);
+              ticket = -1;
+              break;
+            }
+          }
+        }
+        if (ticket >= 0) {
+          const ServeDesc* d = prm.serve_desc + ticket % prm.serve_capacity;
+          reset_state(st, *(volatile const int*)&d->p);
+          ServeOut* o = prm.serve_out + ticket % prm.serve_capacity;
+          o->slot = slot;
+          o->t_start_ns = (long long)globaltimer_ns();
+          __threadfence_system();
+          st_release_sys_i64(&o->claimed, (long long)ticket + 1);
+        }
+        sy->ticket = ticket;
+        __threadfence();
+        st_release_u32(&sy->gen, gen + 1u);
+      } else {
+        const unsigned long long t0 = globaltimer_ns();
+        while (ld_acquire_u32(&sy->gen) == gen) {
+          if (globaltimer_ns() - t0 > (unsigned long long)wait_ns) {
+            atomicExch(&ctl->error, ST_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(200);
+        }
+        ticket = (ld_acquire_u32(&sy->gen) == gen) ? -1 : ldcg(&sy->ticket);
+      }
+      s_ticket = ticket;
+    }
+    __syncthreads();
+    ++gen;
+    const int ticket = s_ticket;
+    if (ticket < 0) return;
+
+    // ---- the request's parameters: the slot's state and workspace ----
+    if (tid == 0) {
+      // the ring entry through volatile loads: the host reuses entries
+      const volatile ServeDesc* d = prm.serve_desc + ticket % prm.serve_capacity;
+      q = prm;
+      q.n = d->n;
+      q.lda = d->lda;
+      q.A = d->A;
+      q.b = d->b;
+      q.x_out = d->x;
+      q.tol = d->tol;
+      q.maxit = d->maxit;
+      q.p = d->p;
+      q.x0 = nullptr;
+      q.X0 = nullptr;
+      q.X_out = nullptr;
+      double* w = prm.X + (size_t)slot * (size_t)prm.serve_ws_stride;
+      const size_t blk = (size_t)prm.serve_ws_stride / 5;
+      q.X = w;
+      q.R = w + blk;
+      q.D0 = w + 2 * blk;
+      q.D1 = w + 3 * blk;
+      q.W = w + 4 * blk;
+      q.part = prm.part + (size_t)slot * C * kPartStride;
+      q.st = st;
+      q.expected_ctas = (unsigned)C;
+      q.group_ctas = C;
+      q.group_rank = rank;
+      q.mode = MODE_SOLVE;
+    }
+    __syncthreads();
+    // the leader's reset of the state is visible: it was fenced before the
+    // ticket went out, and the other CTAs read it after the ticket
+    solve_body<P, true, POL_FP64, false>(q, reinterpret_cast<double*>(dyn_smem), nullptr);
+    __syncthreads();
+
+    // ---- the slot reports the result and frees up ----
+    if (tid == 0) {
+      __threadfence();
+      atom_add_acqrel_u32(&sy->count, 1u);
+      if (rank == 0) {
+        const unsigned long long t0 = globaltimer_ns();
+        bool ok = true;
+        while (ld_acquire_u32(&sy->count) != (unsigned)C) {
+          if (globaltimer_ns() - t0 > (unsigned long long)prm.timeout_ns) {
+            atomicExch(&ctl->error, ST_ERR_TIMEOUT);
+            ok = false;
+            break;
+          }
+        }
+        sy->count = 0u;
+        ServeOut* o = prm.serve_out + ticket % prm.serve_capacity;
+        const int err = *(volatile const int*)&st->error;
+        o->status = !ok ? ST_ERR_TIMEOUT : (err != 0 ? err : *(volatile const int*)&st->result);
+        o->iterations = *(volatile const int*)&st->k;
+        o->relres_true = *(volatile const double*)&st->relres_true;
+        o->t_end_ns = (long long)globaltimer_ns();
+        __threadfence_system();
+        st_release_sys_i64(&o->done, (long long)ticket + 1);
+        atomicSub(&ctl->busy, 1);
+      }
     }
     __syncthreads();
   }
