@@ -211,29 +211,51 @@ __global__ void __launch_bounds__(kThreadsLp, 1)
 }
 
 // ---- fixup: sum partial tiles per row (CTA order), apply scales -----------
+// One block of kBM threads per row tile: the CTA range of the tile is found
+// once, then each thread sums its row's partial rows four columns at a time.
 __global__ void lp_fixup_kernel(LpRun run, int NP, int q, double* __restrict__ W, int ldw) {
+  __shared__ int s_c[2];
   const int64_t n = run.n;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * q) return;
-  const int64_t i = idx / q;
-  const int j = (int)(idx - i * q);
-  const int t = (int)(i / kBM);
-  const int r = (int)(i - (int64_t)t * kBM);
+  const int t = blockIdx.x;
   const int64_t U = run.units;
   const int G = run.ctas;
-  const int64_t lo = (int64_t)t * run.kc, hi = lo + run.kc;
-  // first CTA whose range ends after lo, last whose range starts before hi
-  int c0 = (int)((lo * G) / U);
-  while (c0 > 0 && unit_begin(U, G, c0) > lo) --c0;
-  while (unit_begin(U, G, c0 + 1) <= lo) ++c0;
-  double s = 0.0;
-  for (int c = c0; c < G && unit_begin(U, G, c) < hi; ++c) {
-    if (unit_begin(U, G, c + 1) <= unit_begin(U, G, c)) continue;  // empty range
-    s += (double)run.part[((size_t)(c + t) * kBM + r) * NP + j];
+  if (threadIdx.x == 0) {
+    const int64_t lo = (int64_t)t * run.kc, hi = lo + run.kc;
+    // first CTA whose range ends after lo, last whose range starts before hi
+    int c0 = (int)((lo * G) / U);
+    while (c0 > 0 && unit_begin(U, G, c0) > lo) --c0;
+    while (unit_begin(U, G, c0 + 1) <= lo) ++c0;
+    int c1 = c0;
+    while (c1 + 1 < G && unit_begin(U, G, c1 + 1) < hi) ++c1;
+    s_c[0] = c0;
+    s_c[1] = c1;
   }
-  if (run.row_scale) s *= (double)run.row_scale[i];
-  if (run.col_scale) s *= (double)run.col_scale[j];
-  W[i * ldw + j] = s;
+  __syncthreads();
+  const int r = threadIdx.x;
+  const int64_t i = (int64_t)t * kBM + r;
+  if (i >= n) return;
+  const bool some_empty = U < G;  // with U >= G every CTA holds a unit
+  const double rs = run.row_scale ? (double)run.row_scale[i] : 1.0;
+  for (int j0 = 0; j0 < q; j0 += 4) {
+    double sv[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c = s_c[0]; c <= s_c[1]; ++c) {
+      if (some_empty && unit_begin(U, G, c + 1) <= unit_begin(U, G, c)) continue;
+      const float4 a = *reinterpret_cast<const float4*>(run.part + ((size_t)(c + t) * kBM + r) * NP + j0);
+      sv[0] += (double)a.x;
+      sv[1] += (double)a.y;
+      sv[2] += (double)a.z;
+      sv[3] += (double)a.w;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + u;
+      if (j >= q) break;
+      double v = sv[u];
+      if (run.row_scale) v *= rs;
+      if (run.col_scale) v *= (double)run.col_scale[j];
+      W[i * ldw + j] = v;
+    }
+  }
 }
 
 // ---- conversions -------------------------------------------------------------
@@ -528,8 +550,7 @@ cudaError_t block_product(int kind, int NP, const void* Q, int64_t ldq, const vo
     e = (NP == 16) ? launch_apass_t<KIND_FP8, 16>(tA, tB, run, s)
                    : launch_apass_t<KIND_FP8, 32>(tA, tB, run, s);
   if (e != cudaSuccess) return e;
-  const int64_t tot = n * q;
-  lp_fixup_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(run, NP, q, W, q);
+  lp_fixup_kernel<<<(unsigned)T, kBM, 0, s>>>(run, NP, q, W, q);
   if (ev1) cudaEventRecord(ev1, s);
   return cudaGetLastError();
 }

@@ -1525,11 +1525,15 @@ __device__ __forceinline__ void lp_put(const Params& prm, int j, int64_t i, doub
 // preconv: the operand rows already hold V in the MMA type (written by the
 // D-update, followed by a grid barrier), so the conversion and its barrier
 // are skipped.
-// The fixup hands each finished entry (row i, column j, value of A_lp V with
-// the scales applied) to `epi`; lp_apass below stores it (minus b) in Y.
+// The fixup hands finished entries to `epi` four columns at a time:
+// epi(i, j0, v, cnt) with v[u] the entry (row i, column j0 + u) of A_lp V, the
+// scales applied, u < cnt; lp_apass below stores them (minus b) in Y.
+// cmax (FP8 and sliced kinds; nullable): this CTA's column maxima of |V| as
+// ordered bit patterns, when the caller has them already (no scan of V).
 template <int P, int POL, class Epi>
 __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t r0, int64_t r1,
-                             LpCtx& L, SyncShared* ss, int* s_err, bool preconv, Epi epi) {
+                             LpCtx& L, SyncShared* ss, int* s_err, bool preconv, Epi epi,
+                             const unsigned long long* cmax = nullptr) {
   constexpr int KIND = LpCfg<POL>::KIND;
   constexpr int NP = LpNP<P, POL>::value;
   DevState* st = prm.st;
@@ -1543,17 +1547,20 @@ __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t
     // column maxima of |V| over this CTA's rows, as ordered bit patterns
     // (a NaN stays on top and reaches the check of the column scales)
     __shared__ unsigned long long s_cmax[P];
-    for (int j = tid; j < pk; j += kThreads) s_cmax[j] = 0ull;
-    __syncthreads();
-    for (int idx = tid; idx < (int)nr * pk; idx += kThreads) {
-      const int li = idx / pk;
-      const int j = idx - li * pk;
-      atomicMax(&s_cmax[j],
-                (unsigned long long)__double_as_longlong(fabs(ldcg(V + (r0 + li) * p + j))));
+    if (cmax == nullptr) {
+      for (int j = tid; j < pk; j += kThreads) s_cmax[j] = 0ull;
+      __syncthreads();
+      for (int idx = tid; idx < (int)nr * pk; idx += kThreads) {
+        const int li = idx / pk;
+        const int j = idx - li * pk;
+        atomicMax(&s_cmax[j],
+                  (unsigned long long)__double_as_longlong(fabs(ldcg(V + (r0 + li) * p + j))));
+      }
+      __syncthreads();
+      cmax = s_cmax;
     }
-    __syncthreads();
     for (int j = tid; j < pk; j += kThreads)
-      mypart[kSlotVec + j] = __longlong_as_double((long long)s_cmax[j]);
+      mypart[kSlotVec + j] = __longlong_as_double((long long)cmax[j]);
     const int f = grid_arrive(prm, ss);
     if (f < 0) return false;
     if (f == 1) {
@@ -1681,19 +1688,20 @@ __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t
               if (j0 + u < NP) sv[u] += (double)__ldcg(pr + u);
           }
         }
+        const int cnt = min(4, pk - j0);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int j = j0 + u;
-          if (j >= pk) break;
-          double v = sv[u];
-          if constexpr (KIND == tc::KIND_SLICED) {
-            v *= rs * (double)__ldcg(&st->sigma[j]);
-          } else {
-            if (prm.lp_row_scale) v *= rs;
-            if constexpr (KIND == tc::KIND_FP8) v *= (double)__ldcg(&st->sigma[j]);
+          if (u < cnt) {
+            if constexpr (KIND == tc::KIND_SLICED) {
+              sv[u] *= rs * (double)__ldcg(&st->sigma[j]);
+            } else {
+              if (prm.lp_row_scale) sv[u] *= rs;
+              if constexpr (KIND == tc::KIND_FP8) sv[u] *= (double)__ldcg(&st->sigma[j]);
+            }
           }
-          epi(i, j, v);
         }
+        epi(i, j0, sv, cnt);
       }
     }
     __syncthreads();
@@ -1707,9 +1715,10 @@ __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, 
                          bool preconv = false) {
   const int p = prm.p;
   return lp_apass_epi<P, POL>(prm, V, pk, r0, r1, L, ss, s_err, preconv,
-                              [&](int64_t i, int j, double v) {
-                                if (sub_b) v -= prm.b[i];
-                                Y[i * p + j] = v;
+                              [&](int64_t i, int j0, const double (&v)[4], int cnt) {
+#pragma unroll
+                                for (int u = 0; u < 4; ++u)
+                                  if (u < cnt) Y[i * p + j0 + u] = sub_b ? v[u] - prm.b[i] : v[u];
                               });
 }
 
@@ -1890,6 +1899,13 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
           double* Z = prm.Z;
           double* d = prm.cheb_d;
           double* sr = prm.cheb_s;
+          // FP8: the column maxima of each new d come from the update itself
+          // (two buffers: one feeds the next pass while the other fills)
+          constexpr bool kMax = POL == POL_FP8;
+          __shared__ unsigned long long s_cm[2][P];
+          if (kMax)
+            for (int j = tid; j < 2 * P; j += kThreads) (&s_cm[0][0])[j] = 0ull;
+          __syncthreads();
           const int64_t cnt = (r1 - r0) * pk;
           for (int64_t idx = tid; idx < cnt; idx += kThreads) {
             const int64_t o = (r0 + idx / pk) * p + idx % pk;
@@ -1898,29 +1914,85 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
             d[o] = v;
             Z[o] = v;
             sr[o] = r;
+            if (kMax)
+              atomicMax(&s_cm[0][idx % pk], (unsigned long long)__double_as_longlong(fabs(v)));
           }
           __syncthreads();
           // each step: W = A_lp d ; S -= W ; d = c1 d + c2 S ; Z += d, the update
-          // done on the fixup's entries as they are summed; BF16 / TF32 also
-          // write the next step's operand rows there (no separate conversion)
+          // done on the fixup's entries as they are summed, four columns at a
+          // time; BF16 / TF32 also write the next step's operand rows there (no
+          // separate conversion)
           constexpr bool kConvInFixup = POL == POL_BF16 || POL == POL_TF32X3;
+          const bool vec2 = (p & 1) == 0;
           bool conv = false;
+          int cmb = 0;
           for (int k = 1; k < prm.cheb_steps; ++k) {
             const double rn = 1.0 / (2.0 * sg - rho);
             const double c1 = rn * rho, c2 = 2.0 * rn / de;
             const bool conv_next = kConvInFixup && k + 1 < prm.cheb_steps;
+            unsigned long long* cm_next = s_cm[cmb ^ 1];
+            if (kMax) {
+              for (int j = tid; j < P; j += kThreads) cm_next[j] = 0ull;
+              __syncthreads();
+            }
             const bool ok = lp_apass_epi<P, POL>(
-                prm, d, pk, r0, r1, *L, &ss, &s_err, conv, [&](int64_t i, int j, double w) {
-                  const int64_t o = i * p + j;
-                  const double sv = sr[o] - w;
-                  const double dv = c1 * d[o] + c2 * sv;
-                  sr[o] = sv;
-                  d[o] = dv;
-                  Z[o] += dv;
-                  if (conv_next) lp_put<LpCfg<POL>::KIND, LpNP<P, POL>::value>(prm, j, i, dv);
-                });
+                prm, d, pk, r0, r1, *L, &ss, &s_err, conv,
+                [&](int64_t i, int j0, const double (&w)[4], int cn) {
+                  const int64_t o = i * p + j0;
+                  double sv[4], dv[4], zv[4];
+                  if (vec2 && cn == 4) {
+                    const double2 s01 = *reinterpret_cast<const double2*>(sr + o);
+                    const double2 s23 = *reinterpret_cast<const double2*>(sr + o + 2);
+                    const double2 d01 = *reinterpret_cast<const double2*>(d + o);
+                    const double2 d23 = *reinterpret_cast<const double2*>(d + o + 2);
+                    const double2 z01 = *reinterpret_cast<const double2*>(Z + o);
+                    const double2 z23 = *reinterpret_cast<const double2*>(Z + o + 2);
+                    sv[0] = s01.x; sv[1] = s01.y; sv[2] = s23.x; sv[3] = s23.y;
+                    dv[0] = d01.x; dv[1] = d01.y; dv[2] = d23.x; dv[3] = d23.y;
+                    zv[0] = z01.x; zv[1] = z01.y; zv[2] = z23.x; zv[3] = z23.y;
+                  } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                      if (u < cn) {
+                        sv[u] = sr[o + u];
+                        dv[u] = d[o + u];
+                        zv[u] = Z[o + u];
+                      }
+                  }
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    if (u < cn) {
+                      sv[u] -= w[u];
+                      dv[u] = c1 * dv[u] + c2 * sv[u];
+                      zv[u] += dv[u];
+                      if (conv_next)
+                        lp_put<LpCfg<POL>::KIND, LpNP<P, POL>::value>(prm, j0 + u, i, dv[u]);
+                      if (kMax)
+                        atomicMax(&cm_next[j0 + u],
+                                  (unsigned long long)__double_as_longlong(fabs(dv[u])));
+                    }
+                  }
+                  if (vec2 && cn == 4) {
+                    *reinterpret_cast<double2*>(sr + o) = make_double2(sv[0], sv[1]);
+                    *reinterpret_cast<double2*>(sr + o + 2) = make_double2(sv[2], sv[3]);
+                    *reinterpret_cast<double2*>(d + o) = make_double2(dv[0], dv[1]);
+                    *reinterpret_cast<double2*>(d + o + 2) = make_double2(dv[2], dv[3]);
+                    *reinterpret_cast<double2*>(Z + o) = make_double2(zv[0], zv[1]);
+                    *reinterpret_cast<double2*>(Z + o + 2) = make_double2(zv[2], zv[3]);
+                  } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                      if (u < cn) {
+                        sr[o + u] = sv[u];
+                        d[o + u] = dv[u];
+                        Z[o + u] = zv[u];
+                      }
+                  }
+                },
+                kMax ? s_cm[cmb] : nullptr);
             if (!ok) return;
             rho = rn;
+            cmb ^= 1;
             if (conv_next) {
               // the operand rows of every CTA are complete before the next pass
               asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -2598,11 +2670,16 @@ __device__ int serve_claim(const Params& prm) {
       continue;
     }
     const bool stop = ld_acquire_sys_i32(prm.serve_stop) != 0;
-    const bool idle = globaltimer_ns() - t0 > (unsigned long long)prm.serve_idle_ns;
+    const unsigned long long waited = globaltimer_ns() - t0;
+    const bool idle = waited > (unsigned long long)prm.serve_idle_ns;
     if ((stop || idle) && *(volatile int*)&ctl->busy == 0) {
       atomicExch(&ctl->closing, 1);
       return -1;
     }
+    // other slots are busy, but this one has waited timeout_ns for work: it
+    // leaves (the kernel ends once the others do, and the host launches it
+    // again for new requests)
+    if (waited > (unsigned long long)prm.timeout_ns) return -1;
     __nanosleep(500);
   }
 }
@@ -2619,7 +2696,9 @@ __global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constan
   SlotSync* sy = prm.serve_sync + slot;
   ServeCtl* ctl = prm.serve_ctl;
   DevState* st = prm.st + slot;
-  const long long wait_ns = prm.serve_idle_ns + prm.timeout_ns;
+  // a follower waits at most as long as its leader may wait for work, plus
+  // the time to check the ring entry
+  const long long wait_ns = 2 * prm.timeout_ns + prm.serve_idle_ns;
   unsigned gen = 0;
   for (;;) {
     // ---- the leader claims; the slot learns the ticket ----

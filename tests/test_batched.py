@@ -83,8 +83,8 @@ def test_batched_empty_and_invalid(env):
 @pytest.mark.parametrize("p", [1, 4])
 def test_batched_fp32_refinement_reaches_fp64_accuracy(env, p):
     """Batched FP32 + FP64 refinement: every system reaches the FP64 target
-    (true relative residual <= 1e-10, checked here in NumPy) and its x agrees
-    with the FP64 oracle to the accuracy the residual implies."""
+    (true relative residual <= 1e-10, checked here in NumPy) and every x
+    agrees with the FP64 oracle's to the FP64 bar, 1e-8 relative."""
     torch, ccg, oracle = env["torch"], env["ccg"], env["oracle"]
     rng = np.random.default_rng(10 + p)
     sizes = [int(v) for v in np.round(np.exp(rng.uniform(np.log(8), np.log(400), 120)))]
@@ -102,12 +102,10 @@ def test_batched_fp32_refinement_reaches_fp64_accuracy(env, p):
         assert st[k] == 0, (k, n, st[k], rr[k])
         relres = np.linalg.norm(b - A @ xi) / np.linalg.norm(b)
         assert relres <= 1.01e-10 and abs(relres - rr[k]) <= 1e-12, (k, relres, rr[k])
-        if k % 10 == 0:
-            X0 = oracle.initial_block(n, p, None, 1.0, 0)
-            ref = oracle.ccg(A, b, X0, 1e-10, 10000)
-            cond = np.linalg.cond(A)
-            err = np.linalg.norm(xi - ref["x"]) / np.linalg.norm(ref["x"])
-            assert err <= 4.0 * cond * 1e-10, (k, n, err, cond)
+        X0 = oracle.initial_block(n, p, None, 1.0, 0)
+        ref = oracle.ccg(A, b, X0, 1e-10, 10000)
+        err = np.linalg.norm(xi - ref["x"]) / np.linalg.norm(ref["x"])
+        assert err <= 1e-8, (k, n, err)
 
 
 def test_batched_rejects_tensor_core_precisions(env):

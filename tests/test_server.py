@@ -52,12 +52,24 @@ def requests(torch, count, seed):
     return out
 
 
+def even_ld(torch, A):
+    """A with an even leading dimension (the serving kernel's 16-byte loads)."""
+    n = A.shape[0]
+    if n % 2 == 0:
+        return A
+    Ap = torch.zeros((n, n + 1), dtype=torch.float64, device=A.device)
+    Ap[:, :n] = A
+    return Ap
+
+
 def run_server(ccg, torch, reqs, workers, budget, precision=0, share=16, slots=0):
     srv = ccg.Server(workers=workers, budget_bytes=budget, precision=precision,
                      ctas_per_worker=share, slots=slots, max_n=4096)
     xs = [torch.zeros(b.shape[0], dtype=torch.float64, device="cuda") for _, b, *_ in reqs]
+    # the matrices must stay allocated until their results are in
+    mats = [even_ld(torch, A) if slots else A for A, *_ in reqs]
     for k, (A, b, tol, *_) in enumerate(reqs):
-        assert srv.submit(k, A, b, xs[k], p=8, tol=tol, maxit=50000) == 0
+        assert srv.submit(k, mats[k], b, xs[k], p=8, tol=tol, maxit=50000) == 0
     got = {}
     while len(got) < len(reqs):
         for r in srv.poll(64, wait_ms=200):
@@ -153,17 +165,18 @@ def test_slots_mode_restarts_after_idle_and_respects_budget(env):
     budget = fixed + 2.2 * biggest * biggest * 8 + 16e6  # about two matrices at a time
     srv = ccg.Server(slots=4, budget_bytes=budget, max_n=4096)
     xs = [torch.zeros(b.shape[0], dtype=torch.float64, device="cuda") for _, b, *_ in reqs]
+    mats = [even_ld(torch, A) for A, *_ in reqs]
     got = {}
     for k in range(3):
         A, b, tol, *_ = reqs[k]
-        assert srv.submit(k, A, b, xs[k], p=8, tol=tol, maxit=50000) == 0
+        assert srv.submit(k, mats[k], b, xs[k], p=8, tol=tol, maxit=50000) == 0
     while len(got) < 3:
         for r in srv.poll(64, wait_ms=200):
             got[r["id"]] = r
     time.sleep(0.3)  # the kernel ends on idle; the next requests launch it again
     for k in range(3, 6):
         A, b, tol, *_ = reqs[k]
-        assert srv.submit(k, A, b, xs[k], p=8, tol=tol, maxit=50000) == 0
+        assert srv.submit(k, mats[k], b, xs[k], p=8, tol=tol, maxit=50000) == 0
     while len(got) < 6:
         for r in srv.poll(64, wait_ms=200):
             got[r["id"]] = r
