@@ -102,9 +102,11 @@ typedef struct {
                                    first time it meets it (see
                                    ccg_batch_tuning); 0: keep the table       */
     int mixed_method;           /* mixed precision: CCG_MIXED_AUTO (default:
-                                   preconditioned FP64 cCG for BF16 and FP8,
-                                   refinement for FP32), CCG_MIXED_REFINE or
-                                   CCG_MIXED_PRECOND                          */
+                                   refinement for FP32; for BF16 and FP8,
+                                   refinement as a probe that hands over to
+                                   the preconditioned FP64 cCG when it gains
+                                   less than tenfold per step),
+                                   CCG_MIXED_REFINE or CCG_MIXED_PRECOND      */
     int cheb_degree;            /* CCG_MIXED_PRECOND: products with the
                                    quantised A per preconditioner application;
                                    0 = 32 (FP8, FP32) or 48 (BF16)            */
@@ -260,7 +262,7 @@ int ccg_lowp_block_product(ccg_handle* handle, const ccg_lowp_matrix* m, const d
  * Mixed-precision solve of A x = b (FP64 result) with the quantised copy `lpA`
  * of A on the tensor cores, by cfg.mixed_method:
  *
- * CCG_MIXED_REFINE (auto for FP32): iterative refinement in FP64 around inner
+ * CCG_MIXED_REFINE: iterative refinement in FP64 around inner
  * cCG solves on lpA.  Each step computes the FP64 residual r = b - A x, solves
  * A_lp d = r with p agents to the relative tolerance cfg.inner_tol (the
  * recurrence residual decides), and updates x += d.  The solve stops when
@@ -271,7 +273,12 @@ int ccg_lowp_block_product(ccg_handle* handle, const ccg_lowp_matrix* m, const d
  * A_lp approximates A well enough for the system's conditioning.
  * res->iterations counts inner iterations, res->outer_steps refinement steps.
  *
- * CCG_MIXED_PRECOND (auto for BF16 and FP8): FP64 cCG on A (Algorithm 2 with
+ * CCG_MIXED_AUTO: refinement for FP32.  For BF16 and FP8, refinement with
+ * inner solves of at most 200 iterations, as long as each step gains at least
+ * tenfold; otherwise the preconditioned solve below continues from the best x
+ * (res->iterations and res->outer_steps then add both parts).
+ *
+ * CCG_MIXED_PRECOND: FP64 cCG on A (Algorithm 2 with
  * Algorithm 3's deflation and Algorithm 4's stop rule and residual check) in
  * which each new direction block is built from Z_{k+1} = q(A_lp) R_{k+1}, a
  * Chebyshev polynomial of cfg.cheb_degree products with A_lp on the interval

@@ -2,7 +2,9 @@
 //
 // CCG_MIXED_PRECOND goes to the preconditioned FP64 solve (ccg_capi.cu);
 // CCG_MIXED_REFINE is FP64 iterative refinement around inner cCG solves on a
-// quantised A:
+// quantised A; CCG_MIXED_AUTO with BF16 / FP8 probes with refinement and
+// hands over to the preconditioned solve when it contracts too slowly.
+// Refinement:
 //   x = x0;  r = b - A x (FP64, MODE_REFINE)
 //   repeat:  solve A_lp d = r_s with p agents to a loose relative tolerance,
 //            where r_s = r sqrt(n) / ||r|| (unit-RMS right-hand side, so the
@@ -15,6 +17,7 @@
 // Host code: argument checks, buffers, launches and the outer loop only.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -68,13 +71,14 @@ extern "C" int ccg_solve_mixed(ccg_handle* h, const ccg_lowp_matrix* m, int64_t 
     if (res) res->status = st;
     return st;
   };
-  if (h && m) {
-    const int method = h->cfg.mixed_method != CCG_MIXED_AUTO ? h->cfg.mixed_method
-                       : m->format == CCG_LOWP_FP32          ? CCG_MIXED_REFINE
-                                                             : CCG_MIXED_PRECOND;
-    if (method == CCG_MIXED_PRECOND)
-      return ccg_solve_precond(h, m, n, A, lda, b, x0, p, tol, maxit, x_out, res);
-  }
+  // CCG_MIXED_AUTO with BF16 / FP8: refinement first, as a probe (short
+  // inner solves, at least a tenfold gain per step); if it cannot contract
+  // (the quantised A too coarse for the conditioning), the preconditioned
+  // FP64 solve continues from its best x
+  const bool probe = h && m && h->cfg.mixed_method == CCG_MIXED_AUTO &&
+                     m->format != CCG_LOWP_FP32;
+  if (h && m && h->cfg.mixed_method == CCG_MIXED_PRECOND)
+    return ccg_solve_precond(h, m, n, A, lda, b, x0, p, tol, maxit, x_out, res);
   if (!h || !m || n < 1 || m->n != n || m->device != h->device || p < 1 || p > ccg::kMaxP ||
       p > n || lda < n || !(tol > 0.0) || !std::isfinite(tol) || maxit < 0 || !A || !b || !x_out)
     return fail(CCG_ERR_INVALID);
@@ -227,13 +231,14 @@ extern "C" int ccg_solve_mixed(ccg_handle* h, const ccg_lowp_matrix* m, int64_t 
 
   int status = CCG_NOT_CONVERGED;
   int total = 0, outer = 0, stall = 0, drops = 0, last_agent = 0, last_pf = p;
+  constexpr int kProbeInner = 200;  // inner iterations per probing step
   double last_recur = 0.0;
   if (bnorm == 0.0 || relres <= tol) status = CCG_OK;
   while (status != CCG_OK && outer < max_outer && total < maxit) {
     ++outer;
     // inner tolerance: loose, but not tighter than the outer target needs
     in.tol = std::max(tin, 0.5 * tol / relres);
-    in.maxit = maxit - total;
+    in.maxit = probe ? std::min(kProbeInner, maxit - total) : maxit - total;
     e = run(h, in, P, true, G, pol, p);
     if (e != cudaSuccess) return fail(map_cuda(e));
     const DevState& is = *h->h_state;
@@ -255,7 +260,16 @@ extern "C" int ccg_solve_mixed(ccg_handle* h, const ccg_lowp_matrix* m, int64_t 
     if (e != cudaSuccess) return fail(map_cuda(e));
     if (h->h_state->error != 0) return fail(h->h_state->error);
     rnorm = h->h_state->rnorm;
+    const double prev = relres;
     relres = h->h_state->relres_true;
+    if (probe && !(relres <= 0.1 * prev)) {
+      if (relres < best) {
+        best = relres;
+        e = cudaMemcpyAsync(xbest, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return fail(map_cuda(e));
+      }
+      break;  // refinement contracts too slowly: hand over to the preconditioned solve
+    }
     if (relres < best) {
       best = relres;
       stall = 0;
@@ -286,6 +300,22 @@ extern "C" int ccg_solve_mixed(ccg_handle* h, const ccg_lowp_matrix* m, int64_t 
     res->device_ms = ms;
     res->ctas = G;
     res->outer_steps = outer;
+  }
+  if (probe && status != CCG_OK && total < maxit) {
+    // continue from the refinement's best x with the preconditioned solve;
+    // the counts of both parts add up
+    ccg_result r2;
+    const int st2 = ccg_solve_precond(h, m, n, A, lda, b, x_out, p, tol, maxit - total, x_out,
+                                      &r2);
+    if (res) {
+      const ccg_result r1 = *res;
+      *res = r2;
+      res->iterations += r1.iterations;
+      res->outer_steps += r1.outer_steps;
+      res->drops += r1.drops;
+      res->device_ms += r1.device_ms;
+    }
+    return st2;
   }
   return status;
 }

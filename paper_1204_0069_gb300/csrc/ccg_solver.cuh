@@ -1712,14 +1712,15 @@ __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t
 template <int P, int POL>
 __device__ bool lp_apass(const Params& prm, const double* V, int pk, double* Y, bool sub_b,
                          int64_t r0, int64_t r1, LpCtx& L, SyncShared* ss, int* s_err,
-                         bool preconv = false) {
+                         bool preconv = false, const unsigned long long* cmax = nullptr) {
   const int p = prm.p;
   return lp_apass_epi<P, POL>(prm, V, pk, r0, r1, L, ss, s_err, preconv,
                               [&](int64_t i, int j0, const double (&v)[4], int cnt) {
 #pragma unroll
                                 for (int u = 0; u < 4; ++u)
                                   if (u < cnt) Y[i * p + j0 + u] = sub_b ? v[u] - prm.b[i] : v[u];
-                              });
+                              },
+                              cmax);
 }
 
 // --------------------------------------------------------------------------
@@ -2082,6 +2083,10 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
   // and the next tensor-core A-pass skips its conversion and barrier
   constexpr bool kFuseConv = POL == POL_BF16 || POL == POL_TF32X3;
   bool conv_ready = false;
+  // sliced FP64 policy: the D-update gathers the column maxima of D_{k+1}
+  // over this CTA's rows, so the next A-pass skips its scan of D
+  __shared__ unsigned long long s_dmax[P];
+  bool dmax_ready = false;
   for (;;) {
     if (tid == 0) {
       s_int[0] = ldcg(&st->ctrl);
@@ -2187,8 +2192,10 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     } else if constexpr (POL == POL_F32) {
       if (!apass_f32<P>(prm, D, pk, prm.W, false, r0, r1, &ss, &s_err)) return;
     } else {
-      if (!lp_apass<P, POL>(prm, D, pk, prm.W, false, r0, r1, *L, &ss, &s_err, conv_ready))
+      if (!lp_apass<P, POL>(prm, D, pk, prm.W, false, r0, r1, *L, &ss, &s_err, conv_ready,
+                            dmax_ready ? s_dmax : nullptr))
         return;
+      dmax_ready = false;
     }
     partial_grams<POL == POL_FP64 || POL == POL_SLICED>(D, prm.W, prm.R, D, nullptr, p, pk, r0, r1, mypart, smem, kStageDoubles);
     CCG_SYNC_RED(RED_M_G, pk, (serial_alpha<P, !kExact>(prm, S), serial_pc_clear(prm)));
@@ -2279,6 +2286,11 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         Ts[b * kLd + a] = ldcg(&st->betaT[b * kMaxP + a]);
       }
       __syncthreads();
+      constexpr bool kMaxD = POL == POL_SLICED;
+      if constexpr (kMaxD) {
+        for (int j = tid; j < P; j += kThreads) s_dmax[j] = 0ull;
+        __syncthreads();
+      }
       const int64_t cnt = (r1 - r0) * pk;
       for (int64_t idx = tid; idx < cnt; idx += kThreads) {
         const int64_t i = r0 + idx / pk;
@@ -2289,6 +2301,8 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         const double v = ldcg(prm.R + i * p + a) + acc;
         Dn[i * p + a] = v;
         if constexpr (kFuseConv) lp_put<LpCfg<POL>::KIND, LpNP<P, POL>::value>(prm, a, i, v);
+        if constexpr (kMaxD)
+          atomicMax(&s_dmax[a], (unsigned long long)__double_as_longlong(fabs(v)));
       }
       if constexpr (kFuseConv) {
         // operand rows of the inactive columns stay zero
@@ -2300,7 +2314,15 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
         }
         asm volatile("fence.proxy.async.global;" ::: "memory");
       }
-      if (!grid_barrier(prm, &ss, &s_err)) return;
+      if constexpr (kMaxD) {
+        // no grid barrier: the next A-pass starts with the grid-wide
+        // reduction of the column maxima, its slicing reads this CTA's rows
+        // only, and a grid barrier follows the slicing
+        __syncthreads();
+        dmax_ready = true;
+      } else {
+        if (!grid_barrier(prm, &ss, &s_err)) return;
+      }
       conv_ready = kFuseConv;
       cur ^= 1;
     }

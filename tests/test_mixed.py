@@ -159,3 +159,23 @@ def test_precond_with_prequantised_matrix_and_degree_one(env):
     _, counts, _ = oracle_counts(env["oracle"], A, b, X0, 1e-10, 20 * n)
     assert r.status == 0, r
     assert within_envelope(r.iterations, counts), (r.iterations, counts)
+
+
+@pytest.mark.parametrize("fmt", [2, 3], ids=["bf16", "fp8"])
+def test_auto_method_probes_refinement_then_preconditions(env, fmt):
+    """The default method: on a well-conditioned system refinement converges
+    by itself; on an ill-conditioned kernel it hands over to the
+    preconditioned FP64 solve, which reaches the FP64 bar against the
+    oracle."""
+    A, b = wl.gram_shift(1024, seed=4, shift=0.5 if fmt == 2 else 2.0)
+    r, x = solve(env, A, b, 8, fmt)
+    assert r.status == 0, r
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1.01e-10
+    n = 2048
+    A, b = wl.exp_kernel(n, seed=2, length=0.1, nugget=1e-3)
+    r, x = solve(env, A, b, 8, fmt)
+    assert r.status == 0, r
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1.01e-10
+    ref = env["oracle"].ccg(A, b, env["oracle"].initial_block(n, 8, None, 1.0, 0), 1e-10,
+                            20 * n, nthreads=8)
+    assert np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"]) <= 1e-8
