@@ -50,7 +50,7 @@ GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
 # 11 853.2 MB; sliced product (21 sliced passes and one FP64 check over the
 # FP64 A): 946.8 MB per sliced pass, profiles/sliced_fp64_solve_traffic_n8192_p8.md.
 NCU_BYTES_PER_PASS = {("fp64", 8192, 8): (11814291712 + 45762304) / 22.0,
-                      ("sliced", 8192, 8): (20316387840 + 104307200 - 8.0 * 8192 ** 2) / 21.0}
+                      ("sliced", 8192, 8): (20315822848 + 103993856 - 8.0 * 8192 ** 2) / 21.0}
 
 
 def run_config(n, p, product):
@@ -78,7 +78,8 @@ def parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--maxit", type=int, default=0, help="iteration cap (0 = 20 n)")
     ap.add_argument("--profile", default="none",
-                    choices=["none", "solve", "block", "lowp", "mixed", "lowp32", "sliced"],
+                    choices=["none", "solve", "block", "lowp", "mixed", "lowp32", "sliced",
+                             "cheb", "batched"],
                     help="profiling mode: run only K solves, K FP64 block products or K "
                          "tensor-core block products (n = 32768)")
     ap.add_argument("--no-mixed", action="store_true",
@@ -637,6 +638,50 @@ def main():
         m.close()
         solver.close()
         return
+    if args.profile == "batched":
+        # the batched FP64 solver on the first 512 systems of the batching
+        # family, default A-pass shapes (no autotuning launches)
+        import numpy as np
+        rng = np.random.default_rng(3)
+        sizes = [int(v) for v in np.round(np.exp(rng.uniform(np.log(32), np.log(1024), 512)))]
+        shifts = rng.uniform(0.05, 1.0, 512)
+        a_off, v_off, at, vt = ccg.batch_offsets(sizes)
+        Ap = torch.zeros(at, dtype=torch.float64, device=dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(3)
+        for nn, sh, ao in zip(sizes, shifts, a_off):
+            G = torch.randn(nn, nn, dtype=torch.float64, device=dev, generator=g)
+            blk = Ap[ao:ao + nn * (nn + (nn & 1))].view(nn, nn + (nn & 1))
+            blk[:, :nn] = G @ G.T / nn
+            blk.diagonal().add_(float(sh))
+        bp = torch.randn(vt, dtype=torch.float64, device=dev, generator=g)
+        xb = torch.zeros_like(bp)
+        with ccg.Solver(stream=stream.cuda_stream, batch_autotune=False) as sb:
+            for _ in range(args.warmup + args.steps):
+                summ, st, it, rr = sb.solve_batched(sizes, Ap, bp, xb, p=4, tol=TOL, maxit=20000)
+                print(json.dumps({"status": summ.status_name, "ms": summ.device_ms,
+                                  "iterations": int(np.sum(it)),
+                                  "fp64_flops": float(np.sum(2.0 * np.array(sizes, dtype=float) ** 2
+                                                             * 4 * it))}), flush=True)
+        solver.close()
+        return
+    if args.profile == "cheb":
+        # the preconditioned FP8 solve of the precision family, two FP64
+        # iterations: the launches are solve, preconditioner, solve, ...
+        A32 = device_exp_kernel(args.lowp_n, 2, 0.1, 1e-3, dev)
+        b32 = torch.randn(args.lowp_n, dtype=torch.float64, device=dev)
+        with ccg.Solver(stream=stream.cuda_stream, mixed_method=ccg.MIXED_PRECOND) as sp:
+            m = sp.lowp_matrix(A32, ccg.LOWP_FP8_E4M3)
+            x32 = torch.zeros(args.lowp_n, dtype=torch.float64, device=dev)
+            for _ in range(args.warmup + args.steps):
+                r = sp.solve_mixed(m, A32, b32, x32, p=p, tol=TOL, maxit=2)
+                if r.status not in (0, 1):
+                    raise RuntimeError(f"status {r.status}")
+            m.close()
+        torch.cuda.synchronize()
+        solver.close()
+        print(json.dumps({"profile": "cheb", "n": args.lowp_n, "p": p}))
+        return
     if args.profile == "lowp":
         A32 = device_exp_kernel(args.lowp_n, 2, 0.1, 1e-3, dev)
         m = solver.lowp_matrix(A32, ccg.LOWP_BF16 if args.lowp_fmt == "bf16" else ccg.LOWP_FP8_E4M3)
@@ -782,6 +827,8 @@ def main():
                              ("bf16", ccg.BF16_IR, 0), ("fp8", ccg.FP8_IR, 0),
                              ("fp64_pipe", ccg.FP64, 0), ("fp64_pipe_slots", ccg.FP64, 8)):
             serving[name] = serving_line(ccg, dev, pr, slots=sl)
+        # a longer window of arrivals for the fastest path
+        serving["fp8_400_arrivals"] = serving_line(ccg, dev, ccg.FP8_IR, count=400)
         detail("serving", serving)
         targets["serving_p50_p99_ms"] = {k: [round(v["p50_ms"]), round(v["p99_ms"])]
                                          for k, v in serving.items() if isinstance(v, dict)}
