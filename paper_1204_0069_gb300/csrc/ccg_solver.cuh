@@ -747,34 +747,30 @@ __device__ __forceinline__ double red_get(const DevState* st, int off) {
   return ldcg(&st->red[off]);
 }
 
-// Y <- L^{-T} L^{-1} Y for the m columns of y, L lower (m x m, m <= NB).
+// Y <- L^{-T} L^{-1} Y for the m columns of y, L lower (m x m, m <= 32).
 // One warp per right-hand side: lane a holds entry a of the column in a
 // register; each solved entry is broadcast by a shuffle and applied to the
 // remaining rows at once, so the dependent chain per row is a shuffle, a
-// multiplication by the pivot reciprocal and an FMA.  rinv: shared scratch
-// for the m pivot reciprocals.
-template <int NB>
+// multiplication by the pivot reciprocal and an FMA.  The row loops stay
+// rolled (a compact body the instruction cache keeps across rows).  rinv:
+// shared scratch for the m pivot reciprocals.
 __device__ void chol_solve_cols(const double* l, double* y, int m, double* rinv) {
   const int lane = threadIdx.x & 31;
   if ((int)threadIdx.x < m) rinv[threadIdx.x] = 1.0 / l[threadIdx.x * kLd + threadIdx.x];
   __syncthreads();
   for (int c = threadIdx.x >> 5; c < m; c += kWarps) {  // warp-uniform
     double v = lane < m ? y[lane * kLd + c] : 0.0;
-#pragma unroll
-    for (int u = 0; u < NB; ++u) {
-      if (u < m) {
-        const double yu = __shfl_sync(0xffffffffu, v, u) * rinv[u];
-        const double lau = (lane > u && lane < m) ? l[lane * kLd + u] : 0.0;
-        v = (lane == u) ? yu : (lane > u ? fma(-lau, yu, v) : v);
-      }
+#pragma unroll 1
+    for (int u = 0; u < m; ++u) {
+      const double yu = __shfl_sync(0xffffffffu, v, u) * rinv[u];
+      const double lau = (lane > u && lane < m) ? l[lane * kLd + u] : 0.0;
+      v = (lane == u) ? yu : (lane > u ? fma(-lau, yu, v) : v);
     }
-#pragma unroll
-    for (int u = NB - 1; u >= 0; --u) {
-      if (u < m) {
-        const double yu = __shfl_sync(0xffffffffu, v, u) * rinv[u];
-        const double lua = (lane < u) ? l[u * kLd + lane] : 0.0;
-        v = (lane == u) ? yu : (lane < u ? fma(-lua, yu, v) : v);
-      }
+#pragma unroll 1
+    for (int u = m - 1; u >= 0; --u) {
+      const double yu = __shfl_sync(0xffffffffu, v, u) * rinv[u];
+      const double lua = (lane < u) ? l[u * kLd + lane] : 0.0;
+      v = (lane == u) ? yu : (lane < u ? fma(-lua, yu, v) : v);
     }
     if (lane < m) y[lane * kLd + c] = v;
   }
@@ -825,61 +821,62 @@ __device__ void stop_test(const Params& prm, SerialSmem& S, int pk, int where) {
 }
 
 // Right-looking Cholesky of the unit-diagonal scaled M (lower triangle in
-// S.l) by one warp: lane i holds row i in registers, column j's multipliers
-// reach the other lanes by shuffles.  Columns are taken in agent order; a
-// column whose pivot is below rank_tol is skipped (agent dropped, Algorithm
-// 3), a pivot below -sqrt(rank_tol) means A is not SPD.  Leaves the factor in
-// S.l, the kept columns in S.keep, their count in S.chol_m and 0 / 2 (not
-// SPD) / 3 (NaN) in S.chol_fail.  Called by warp 0 only.
-template <int NB, bool FAST>
+// S.l) by one warp: lane i updates row i of S.l in place, and the
+// multipliers of column j are read back from shared memory.  The column loop
+// stays rolled: the step runs once per iteration on a single warp, right
+// after the product pass has filled the instruction cache with its own code,
+// and a compact body is fetched once instead of once per column.  Columns are
+// taken in agent order; a column whose pivot is below rank_tol is skipped
+// (agent dropped, Algorithm 3), a pivot below -sqrt(rank_tol) means A is not
+// SPD.  Leaves the factor in S.l, the kept columns in S.keep, their count in
+// S.chol_m and 0 / 2 (not SPD) / 3 (NaN) in S.chol_fail.  Called by warp 0
+// only.
+template <bool FAST>
 __device__ void warp_chol(const Params& prm, SerialSmem& S, int pk) {
   const int lane = threadIdx.x & 31;
-  double r[NB];
-#pragma unroll
-  for (int k = 0; k < NB; ++k)
-    r[k] = (lane < pk && k <= lane) ? S.l[lane * kLd + k] : 0.0;
+  double* row = S.l + lane * kLd;
+  const bool mine = lane < pk;
   const double neg_lim = -sqrt(prm.rank_tol);
   int m = 0, fail = 0;
-#pragma unroll
-  for (int j = 0; j < NB; ++j) {
-    if (j < pk && fail == 0) {
-      const double d = __shfl_sync(0xffffffffu, r[j], j);
-      int decision = 0;  // 0 keep, 1 drop, 2 not SPD, 3 NaN
-      if (S.m[j * kLd + j] == 0.0) decision = 1;  // zero direction
-      else if (!(d == d)) decision = 3;
-      else if (d < neg_lim) decision = 2;
-      else if (d < prm.rank_tol) decision = 1;
-      if (decision >= 2) {
-        fail = decision;
-      } else if (decision == 0) {
-        // square root and division as in the textbook factorisation: the
-        // iteration count of an ill-conditioned solve follows the rounding of
-        // the factor (a reciprocal square root moved it by 9 of 388 at
-        // n = 8192, p = 8)
-        if constexpr (FAST) {
-          // inner solves: one reciprocal square root per column (shorter
-          // dependent chain; the refinement does not see the rounding)
-          const double rj = rsqrt(d);
-          if (lane == j) r[j] = d * rj;
-          else if (lane > j) r[j] = r[j] * rj;
-        } else {
-          const double ljj = sqrt(d);
-          if (lane == j) r[j] = ljj;
-          else if (lane > j) r[j] = r[j] / ljj;
-        }
-#pragma unroll
-        for (int k = j + 1; k < NB; ++k) {
-          const double lkj = __shfl_sync(0xffffffffu, r[j], k);
-          if (lane >= k) r[k] -= r[j] * lkj;
-        }
-        if (lane == 0) S.keep[m] = j;
-        ++m;
-      }
+#pragma unroll 1
+  for (int j = 0; j < pk; ++j) {
+    __syncwarp();
+    const double d = S.l[j * kLd + j];
+    int decision = 0;  // 0 keep, 1 drop, 2 not SPD, 3 NaN
+    if (S.m[j * kLd + j] == 0.0) decision = 1;  // zero direction
+    else if (!(d == d)) decision = 3;
+    else if (d < neg_lim) decision = 2;
+    else if (d < prm.rank_tol) decision = 1;
+    if (decision >= 2) {
+      fail = decision;
+      break;
     }
+    if (decision == 1) continue;
+    double lij = 0.0;
+    if constexpr (FAST) {
+      // inner solves: one reciprocal square root per column (shorter
+      // dependent chain; the refinement does not see the rounding)
+      const double rj = rsqrt(d);
+      if (lane == j) row[j] = d * rj;
+      else if (lane > j && mine) row[j] = lij = row[j] * rj;
+    } else {
+      // square root and division as in the textbook factorisation: the
+      // iteration count of an ill-conditioned solve follows the rounding of
+      // the factor (a reciprocal square root moved it by 9 of 388 at
+      // n = 8192, p = 8)
+      const double ljj = sqrt(d);
+      if (lane == j) row[j] = ljj;
+      else if (lane > j && mine) row[j] = lij = row[j] / ljj;
+    }
+    __syncwarp();
+    if (lane > j && mine) {
+#pragma unroll 4
+      for (int k = j + 1; k <= lane; ++k) row[k] = fma(-lij, S.l[k * kLd + j], row[k]);
+    }
+    if (lane == 0) S.keep[m] = j;
+    ++m;
   }
-#pragma unroll
-  for (int k = 0; k < NB; ++k)
-    if (lane < pk && k <= lane) S.l[lane * kLd + k] = r[k];
+  __syncwarp();
   if (lane == 0) {
     S.chol_m = m;
     S.chol_fail = fail;
@@ -932,7 +929,7 @@ __device__ void serial_alpha(const Params& prm, SerialSmem& S) {
     else if (c == a) S.l[a * kLd + a] = 1.0;
   }
   __syncthreads();
-  if (tid < 32) warp_chol<NB, FAST>(prm, S, pk);
+  if (tid < 32) warp_chol<FAST>(prm, S, pk);
   __syncthreads();
   const int m = S.chol_m;
   if (S.chol_fail) {
@@ -960,7 +957,7 @@ __device__ void serial_alpha(const Params& prm, SerialSmem& S) {
     S.l[a * kLd + c] = S.sc[S.keep[a]] * S.g[S.keep[c] * kLd + S.keep[a]];
   }
   __syncthreads();
-  chol_solve_cols<NB>(S.m, S.l, m, S.sv);
+  chol_solve_cols(S.m, S.l, m, S.sv);
   for (int e = tid; e < m * m; e += kThreads) {
     const int b = e / m, a = e - b * m;
     const double v = -S.sc[S.keep[b]] * S.l[b * kLd + a];
@@ -1027,7 +1024,7 @@ __device__ void serial_beta(const Params& prm, SerialSmem& S) {
     __syncthreads();
     return;
   }
-  chol_solve_cols<NB>(S.m, S.l, pk, S.sv);
+  chol_solve_cols(S.m, S.l, pk, S.sv);
   for (int e = tid; e < sq; e += kThreads) {
     const int b = e / pk, a = e - b * pk;
     const double v = -S.sc[b] * S.l[b * kLd + a];
@@ -1082,7 +1079,7 @@ __device__ void serial_beta_pc(const Params& prm, SerialSmem& S) {
     __syncthreads();
     return;
   }
-  chol_solve_cols<NB>(S.m, S.l, pk, S.sv);
+  chol_solve_cols(S.m, S.l, pk, S.sv);
   for (int e = tid; e < sq; e += kThreads) {
     const int b = e / pk, a = e - b * pk;
     const double v = -S.sc[b] * S.l[b * kLd + a];
