@@ -11,6 +11,9 @@ namespace ccg {
 constexpr int kMaxP = 32;          // agents per solve (warp width)
 constexpr int kThreads = 256;      // threads per CTA of the persistent kernel
 constexpr int kWarps = kThreads / 32;
+// SM sub-partitions, one FP64 pipe each (warp w issues on sub-partition
+// w mod 4); FP64-bound work that needs few warps uses one per sub-partition
+constexpr int kSubParts = 4;
 constexpr int kSq = kMaxP * kMaxP;
 // Per-CTA partial-sum slot: two p x p Grams, one p-vector, one scalar, each
 // entry as an unevaluated sum hi + lo (compensated accumulation): hi at

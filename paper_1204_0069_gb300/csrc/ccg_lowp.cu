@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(kThreadsLp, 1)
       int stage = 0;
       uint32_t phase = 0;
       int64_t u_issued = u0;
+      const uint64_t pol_a = l2_policy_evict_first(), pol_b = l2_policy_evict_last();
       for (int64_t u = u0; u < u1; ++u) {
         if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, run.timeout_ns, err)) break;
         u_issued = u + 1;
@@ -115,8 +116,9 @@ __global__ void __launch_bounds__(kThreadsLp, 1)
         const int k = (int)(u % kc);
         const uint32_t fb = smem_u32(&full[stage]);
         mbar_expect_tx(fb, kStageBytes);
-        tma_load_2d(smem_u32(sA + stage * kTileABytes), &tmA, k * run.k_elems, t * kBM, fb);
-        tma_load_2d(smem_u32(sB + stage * kTileBBytes), &tmB, k * run.k_elems, 0, fb);
+        tma_load_2d_hint(smem_u32(sA + stage * kTileABytes), &tmA, k * run.k_elems, t * kBM, fb,
+                         pol_a);
+        tma_load_2d_hint(smem_u32(sB + stage * kTileBBytes), &tmB, k * run.k_elems, 0, fb, pol_b);
         if (++stage == kStages) { stage = 0; phase ^= 1u; }
       }
       // drain: the last copy issued on every stage has landed before the CTA

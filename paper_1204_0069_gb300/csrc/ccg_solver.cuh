@@ -730,13 +730,17 @@ __device__ __forceinline__ double warp_sum_parts(const Params& prm, int off) {
   return COMP ? __dadd_rn(t.hi, t.lo) : t.hi;
 }
 
-// Entries w0 + j * wstride (j = 0, 1, ...) of the set, one per warp of this
-// CTA.  COMP: compensated (FP64 solves); plain FP64 sums for the inner solves
-// of the mixed-precision paths, whose partials are plain sums already.
+// Entries w0 + j * wstride (j = 0, 1, ...) of the set, one per warp of the
+// first nw warps of this CTA.  COMP: compensated (FP64 solves); plain FP64
+// sums for the inner solves of the mixed-precision paths, whose partials are
+// plain sums already.
 template <bool COMP>
-__device__ void reduce_entries(const Params& prm, int set, int q, int w0, int wstride) {
+__device__ void reduce_entries(const Params& prm, int set, int q, int w0, int wstride,
+                               int nw = kWarps) {
   const int E = red_count(set, q);
-  for (int e = w0 + (int)(threadIdx.x >> 5); e < E; e += wstride) {
+  const int w = (int)(threadIdx.x >> 5);
+  if (w >= nw) return;
+  for (int e = w0 + w; e < E; e += wstride) {
     const int off = red_slot(set, q, e);
     const double v = warp_sum_parts<COMP>(prm, off);
     if ((threadIdx.x & 31) == 0) prm.st->red[off] = v;
@@ -1329,6 +1333,7 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
       asm volatile("fence.proxy.async.global;" ::: "memory");
       int stage = L.sh->p_stage;
       uint32_t phase = L.sh->p_phase;
+      const uint64_t pol_a = tc::l2_policy_evict_first(), pol_b = tc::l2_policy_evict_last();
       for (int64_t u = u0; u < u1; ++u) {
         if (!tc::mbar_wait(tc::smem_u32(&empty[stage]), phase ^ 1u, to, err)) break;
         const int t = (int)(u / kc);
@@ -1341,10 +1346,10 @@ __device__ void lp_pass(const Params& prm, LpCtx& L) {
         }
         const uint32_t fb = tc::smem_u32(&full[stage]);
         tc::mbar_expect_tx(fb, S::kStageBytes);
-        tc::tma_load_2d(tc::smem_u32(sA + stage * tc::kTileABytes), &prm.lp_tmA,
-                        k * prm.lp_kelems, ty * tc::kBM, fb);
-        tc::tma_load_2d(tc::smem_u32(sB + stage * S::kTileBBytes), &prm.lp_tmB,
-                        k * prm.lp_kelems, 0, fb);
+        tc::tma_load_2d_hint(tc::smem_u32(sA + stage * tc::kTileABytes), &prm.lp_tmA,
+                             k * prm.lp_kelems, ty * tc::kBM, fb, pol_a);
+        tc::tma_load_2d_hint(tc::smem_u32(sB + stage * S::kTileBBytes), &prm.lp_tmB,
+                             k * prm.lp_kelems, 0, fb, pol_b);
         L.sh->issued[stage] = (int)phase;
         if (++stage == ST) { stage = 0; phase ^= 1u; }
       }
@@ -1824,7 +1829,8 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
     const bool spread_ = G > 1 && red_count(SET, q_) > kRedLocalMax;         \
     if (spread_) {                                                           \
       if (!grid_barrier(prm, &ss, &s_err)) return;                           \
-      reduce_entries<kExact>(prm, SET, q_, cta * kWarps, G * kWarps);                \
+      reduce_entries<kExact>(prm, SET, q_, cta * kSubParts, G * kSubParts,     \
+                             kSubParts);                                     \
     }                                                                        \
     const int f_ = grid_arrive(prm, &ss);                                    \
     if (f_ < 0) return;                                                      \
