@@ -496,11 +496,17 @@ __device__ void partial_grams(const double* U0, const double* V0, const double* 
   const int groups = kThreads / T;
   const int gi = threadIdx.x / T, q = threadIdx.x % T;
   // When they fit, the CTA's rows of the operand blocks (first pk columns)
-  // are read once, coalesced, into shared memory (U0 V0 U1 V1 S in order)
+  // are read once, coalesced, into shared memory (U0 V0 U1 V1 S in order).
+  // The exact sums stage each value decoded for the accumulator (one word of
+  // significand and sign, a 16-bit exponent): every value enters pk products.
   const int64_t nr = r1 - r0;
   const int64_t blk = nr * pk;
   const int nblk = (U0 ? 2 : 0) + (U1 ? 2 : 0) + (S ? 1 : 0);
-  const bool staged = stage != nullptr && nblk * blk <= stage_doubles;
+  constexpr int kStageBytesPer = COMP ? 10 : 8;
+  const bool staged =
+      stage != nullptr && nblk * blk * kStageBytesPer <= (int64_t)stage_doubles * 8;
+  unsigned long long* st_m = reinterpret_cast<unsigned long long*>(stage);
+  short* st_e = staged ? reinterpret_cast<short*>(st_m + nblk * blk) : nullptr;
   const int oU1 = U0 ? 2 * (int)blk : 0;
   const int oS = oU1 + (U1 ? 2 * (int)blk : 0);
   if (staged) {
@@ -525,7 +531,15 @@ __device__ void partial_grams(const double* U0, const double* V0, const double* 
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int g = g0 + u * kThreads;
-        if (g < tot) stage[g] = v[u];
+        if (g < tot) {
+          if constexpr (COMP) {
+            int e;
+            xacc_decode(v[u], st_m[g], e);
+            st_e[g] = (short)e;
+          } else {
+            stage[g] = v[u];
+          }
+        }
       }
     }
     __syncthreads();
@@ -550,22 +564,27 @@ __device__ void partial_grams(const double* U0, const double* V0, const double* 
     if (act && staged) {
       const int ou = e < n0 ? 0 : e < n0 + n1 ? oU1 : oS;
       const int ov = e < n0 + n1 ? ou + (int)blk : oS;
-      const double* Us = stage + ou + a;
-      const double* Vs = stage + ov + c;
-      XAcc x;
-      xacc_init(x);
       if constexpr (COMP) {
-        int K = 2;
-        for (int rr = q; rr < (int)nr; rr += T) K = max(K, xacc_expsum(Us[rr * pk], Vs[rr * pk]));
+        const unsigned long long* Um = st_m + ou + a;
+        const unsigned long long* Vm = st_m + ov + c;
+        const short* Ue = st_e + ou + a;
+        const short* Ve = st_e + ov + c;
+        XAcc x;
+        xacc_init(x);
+        int K = 2;  // anchor: the largest exponent sum of the entry's terms
+#pragma unroll 8
+        for (int rr = q; rr < (int)nr; rr += T) K = max(K, (int)Ue[rr * pk] + (int)Ve[rr * pk]);
         x.K = K;
-      }
 #pragma unroll 4
-      for (int rr = q; rr < (int)nr; rr += T) {
-        const double uu = Us[rr * pk], vv = Vs[rr * pk];
-        if constexpr (COMP) xacc_fma_k(x, uu, vv);
-        else t.hi = fma(uu, vv, t.hi);
+        for (int rr = q; rr < (int)nr; rr += T)
+          xacc_fma_kd(x, Um[rr * pk], Vm[rr * pk], (int)Ue[rr * pk] + (int)Ve[rr * pk]);
+        t = xacc_value(x);
+      } else {
+        const double* Us = stage + ou + a;
+        const double* Vs = stage + ov + c;
+#pragma unroll 4
+        for (int rr = q; rr < (int)nr; rr += T) t.hi = fma(Us[rr * pk], Vs[rr * pk], t.hi);
       }
-      if constexpr (COMP) t = xacc_value(x);
     } else if (act) {
       XAcc x;
       xacc_init(x);

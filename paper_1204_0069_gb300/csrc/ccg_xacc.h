@@ -167,17 +167,25 @@ CCG_XHD int xacc_expsum(double x, double y) {
   const int ey = (int)(xacc_bits(y) >> 52) & 0x7FF;
   return xacc_max(ex, 1) + xacc_max(ey, 1);
 }
-// As xacc_fma with the anchor fixed beforehand (a.K >= every term's exponent
-// sum): no re-anchoring and no branches, so unrolled terms interleave.  The
-// product P enters as (P 2^53) >> (K - e), shifted by whole words and then
-// bits with selects, and is added or subtracted through its two's complement.
-CCG_XHD void xacc_fma_k(XAcc& a, double x, double y) {
-  const unsigned long long bx = xacc_bits(x), by = xacc_bits(y);
-  const int ex = (int)(bx >> 52) & 0x7FF, ey = (int)(by >> 52) & 0x7FF;
-  a.bad |= (int)((ex == 0x7FF) | (ey == 0x7FF));
-  const unsigned long long mx = (bx & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(ex != 0) << 52);
-  const unsigned long long my = (by & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(ey != 0) << 52);
-  const int sh = a.K - (xacc_max(ex, 1) + xacc_max(ey, 1));
+// An operand decoded once for many products: its significand with the hidden
+// bit (bits 0-52) and its sign (bit 63) in one word, and its exponent (max(e,
+// 1); 4096 for Inf and NaN, so that the exponent sum of any product with it
+// is at least 4096 while finite sums stay below 4093).
+CCG_XHD void xacc_decode(double x, unsigned long long& m, int& e) {
+  const unsigned long long bx = xacc_bits(x);
+  const int ex = (int)(bx >> 52) & 0x7FF;
+  m = (bx & 0x800FFFFFFFFFFFFFull) | ((unsigned long long)(ex != 0) << 52);
+  e = ex == 0x7FF ? 4096 : xacc_max(ex, 1);
+}
+// w += x y for decoded operands with exponent sum s, the anchor fixed
+// beforehand (a.K >= every finite term's exponent sum): no re-anchoring and no
+// branches, so unrolled terms interleave.  The product P enters as
+// (P 2^53) >> (K - s), shifted by whole words and then bits with selects, and
+// is added or subtracted through its two's complement.
+CCG_XHD void xacc_fma_kd(XAcc& a, unsigned long long bx, unsigned long long by, int s) {
+  a.bad |= (int)(s >= 4096);
+  const unsigned long long mx = bx & 0x1FFFFFFFFFFFFFull, my = by & 0x1FFFFFFFFFFFFFull;
+  const int sh = a.K - s;
   const unsigned long long plo = mx * my, phi = xacc_mulhi(mx, my);
   const unsigned long long q0 = plo << 53, q1 = (phi << 53) | (plo >> 11), q2 = phi >> 11;
   const int ws = xacc_min(sh >> 6, 3), bs = sh & 63;
@@ -191,6 +199,14 @@ CCG_XHD void xacc_fma_k(XAcc& a, double x, double y) {
   xacc_add3(a, r0, r1, r2);
   xacc_add3(a, m & 1ull, 0ull, 0ull);
 }
+// As xacc_fma with the anchor fixed beforehand, from the doubles themselves.
+CCG_XHD void xacc_fma_k(XAcc& a, double x, double y) {
+  unsigned long long mx, my;
+  int ex, ey;
+  xacc_decode(x, mx, ex);
+  xacc_decode(y, my, ey);
+  xacc_fma_kd(a, mx, my, ex + ey);
+}
 // 53 bits of the magnitude m starting at bit pos (zeros below bit 0)
 CCG_XHD unsigned long long xacc_bits53(const unsigned long long m[3], int pos) {
   const unsigned long long kMask = (1ull << 53) - 1ull;
@@ -200,6 +216,28 @@ CCG_XHD unsigned long long xacc_bits53(const unsigned long long m[3], int pos) {
   const unsigned long long lo = m[limb];
   const unsigned long long hi = limb < 2 ? m[limb + 1] : 0ull;
   return (off ? (lo >> off) | (hi << (64 - off)) : lo) & kMask;
+}
+CCG_XHD double xacc_from_bits(unsigned long long u) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  std::memcpy(&x, &u, sizeof x);
+  return x;
+#endif
+}
+// (-1)^sign m 2^s for an integer m < 2^53 (sgn: the sign bit).  A normal
+// result is assembled from its bit fields (exact; integer operations only,
+// where a conversion and ldexp cost several operations on the slow FP64
+// pipe); a subnormal or overflowing one goes through ldexp, which rounds it.
+CCG_XHD double xacc_scaled(unsigned long long m, int s, unsigned long long sgn) {
+  if (m == 0ull) return xacc_from_bits(sgn);
+  const int z = xacc_clz(m) - 11;    // leading zeros within the 53-bit field
+  const int e = s + 52 - z + 1023;   // biased exponent once normalised
+  if (e >= 1 && e <= 2046)
+    return xacc_from_bits(sgn | ((unsigned long long)e << 52) | ((m << z) & 0xFFFFFFFFFFFFFull));
+  const double v = ldexp((double)m, s);
+  return sgn ? -v : v;
 }
 CCG_XHD DSum xacc_value(const XAcc& a) {
   if (a.bad) return DSum{NAN, 0.0};
@@ -217,9 +255,9 @@ CCG_XHD DSum xacc_value(const XAcc& a) {
   else if (m[1]) b = 127 - xacc_clz(m[1]);
   else if (m[0]) b = 63 - xacc_clz(m[0]);
   else return DSum{0.0, 0.0};
-  const double hi = ldexp((double)xacc_bits53(m, b - 52), b - 52 + a.K - 2203);
-  const double lo = ldexp((double)xacc_bits53(m, b - 105), b - 105 + a.K - 2203);
-  return neg ? DSum{-hi, -lo} : DSum{hi, lo};
+  const unsigned long long sgn = neg ? 0x8000000000000000ull : 0ull;
+  return DSum{xacc_scaled(xacc_bits53(m, b - 52), b - 52 + a.K - 2203, sgn),
+              xacc_scaled(xacc_bits53(m, b - 105), b - 105 + a.K - 2203, sgn)};
 }
 
 }  // namespace ccg

@@ -39,12 +39,17 @@ def xdot(tmp_path_factory):
     lib = ctypes.CDLL(str(out))
     lib.xacc_dot.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long, ctypes.c_int,
                              ctypes.c_void_p]
+    lib.xacc_dot_ldexp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long,
+                                   ctypes.c_void_p]
 
     def run(x, y, fixed):
         x = np.ascontiguousarray(x, dtype=np.float64)
         y = np.ascontiguousarray(y, dtype=np.float64)
         o = np.zeros(2)
-        lib.xacc_dot(x.ctypes.data, y.ctypes.data, x.size, int(fixed), o.ctypes.data)
+        if fixed == "ldexp":
+            lib.xacc_dot_ldexp(x.ctypes.data, y.ctypes.data, x.size, o.ctypes.data)
+        else:
+            lib.xacc_dot(x.ctypes.data, y.ctypes.data, x.size, int(fixed), o.ctypes.data)
         return float(o[0]), float(o[1])
     return run
 
@@ -131,3 +136,26 @@ def test_both_variants_agree_inside_the_window(xdot):
         x = rng.standard_normal(n) * np.exp(rng.uniform(-20, 20, n))
         y = rng.standard_normal(n) * np.exp(rng.uniform(-20, 20, n))
         assert xdot(x, y, False) == xdot(x, y, True)
+
+
+def test_bit_fields_match_the_ldexp_route(xdot):
+    """hi and lo are assembled from their bit fields when normal; the same
+    numbers written as (double) m * 2^s with ldexp must come out bit for bit,
+    across the normal range, subnormal parts (rounded by ldexp on both
+    routes), signed zeros and overflow to infinity."""
+    rng = np.random.default_rng(21)
+    sets = list(cases())
+    for _ in range(200):
+        n = int(rng.integers(1, 40))
+        span = float(rng.choice([1.0, 40.0, 300.0]))
+        scale = float(rng.choice([1.0, 1e-150, 1e-160, 1e-165, 1e150, 1e154]))
+        x = rng.standard_normal(n) * np.exp(rng.uniform(-span, span, n)) * scale
+        y = rng.standard_normal(n) * np.exp(rng.uniform(-span, span, n))
+        sets.append((x, y))
+    sets.append(([1e-160], [-1e-160]))            # lo part subnormal, negative
+    sets.append(([1.7e308], [4.0]))               # overflows to infinity
+    sets.append(([3.0, -3.0], [5.0, 5.0]))        # exact zero
+    for x, y in sets:
+        got = np.array(xdot(x, y, False))
+        ref = np.array(xdot(x, y, "ldexp"))
+        assert got.tobytes() == ref.tobytes() or (np.isnan(got[0]) and np.isnan(ref[0])), (got, ref)
