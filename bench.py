@@ -50,7 +50,7 @@ GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
 # 11 853.2 MB; sliced product (21 sliced passes and one FP64 check over the
 # FP64 A): 946.8 MB per sliced pass, profiles/sliced_fp64_solve_traffic_n8192_p8.md.
 NCU_BYTES_PER_PASS = {("fp64", 8192, 8): (11814291712 + 45762304) / 22.0,
-                      ("sliced", 8192, 8): (20315822848 + 103993856 - 8.0 * 8192 ** 2) / 21.0}
+                      ("sliced", 8192, 8): (20263912960 + 66062080 - 8.0 * 8192 ** 2) / 21.0}
 
 
 def run_config(n, p, product):
