@@ -1551,12 +1551,17 @@ __device__ __forceinline__ void lp_put(const Params& prm, int j, int64_t i, doub
 // scales applied, u < cnt; lp_apass below stores them (minus b) in Y.
 // cmax (FP8 and sliced kinds; nullable): this CTA's column maxima of |V| as
 // ordered bit patterns, when the caller has them already (no scan of V).
-template <int P, int POL, class Epi>
-__device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t r0, int64_t r1,
+// VT = float (FP8 kind only): V is an FP32 block; the operand split, the
+// fixup sums and the entries handed to epi are FP32, and cmax holds FP32 bit
+// patterns.
+template <int P, int POL, class Epi, class VT = double>
+__device__ bool lp_apass_epi(const Params& prm, const VT* V, int pk, int64_t r0, int64_t r1,
                              LpCtx& L, SyncShared* ss, int* s_err, bool preconv, Epi epi,
                              const unsigned long long* cmax = nullptr) {
   constexpr int KIND = LpCfg<POL>::KIND;
   constexpr int NP = LpNP<P, POL>::value;
+  constexpr bool kF32 = std::is_same<VT, float>::value;
+  static_assert(!kF32 || KIND == tc::KIND_FP8, "FP32 operand blocks: FP8 kind only");
   DevState* st = prm.st;
   const int p = prm.p;
   const int tid = threadIdx.x;
@@ -1574,14 +1579,18 @@ __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t
       for (int idx = tid; idx < (int)nr * pk; idx += kThreads) {
         const int li = idx / pk;
         const int j = idx - li * pk;
-        atomicMax(&s_cmax[j],
-                  (unsigned long long)__double_as_longlong(fabs(ldcg(V + (r0 + li) * p + j))));
+        const VT v = __ldcg(V + (r0 + li) * p + j);
+        if constexpr (kF32)
+          atomicMax(&s_cmax[j], (unsigned long long)__float_as_uint(fabsf(v)));
+        else
+          atomicMax(&s_cmax[j], (unsigned long long)__double_as_longlong(fabs(v)));
       }
       __syncthreads();
       cmax = s_cmax;
     }
     for (int j = tid; j < pk; j += kThreads)
-      mypart[kSlotVec + j] = __longlong_as_double((long long)cmax[j]);
+      mypart[kSlotVec + j] = kF32 ? (double)__uint_as_float((unsigned)cmax[j])
+                                  : __longlong_as_double((long long)cmax[j]);
     const int f = grid_arrive(prm, ss);
     if (f < 0) return false;
     if (f == 1) {
@@ -1620,23 +1629,30 @@ __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t
     // operand row j (< NP) holds column j of V, zero beyond pk; a thread
     // takes whole rows of V (contiguous reads), the byte rows are written
     // across consecutive threads
-    __shared__ double s_inv[32];  // FP8: 1 / sigma_j
+    __shared__ VT s_inv[32];  // FP8: 1 / sigma_j
     if constexpr (KIND == tc::KIND_FP8) {
       for (int j = tid; j < NP; j += kThreads)
-        s_inv[j] = j < pk ? 1.0 / (double)__ldcg(&st->sigma[j]) : 0.0;
+        s_inv[j] = j < pk ? VT(1) / (VT)__ldcg(&st->sigma[j]) : VT(0);
       __syncthreads();
     }
     for (int li = tid; li < (int)nr; li += kThreads) {
       const int64_t i = r0 + li;
-      const double* vr = V + i * p;
+      const VT* vr = V + i * p;
 #pragma unroll 4
       for (int j = 0; j < NP; ++j) {
-        const double v = (j < pk) ? ldcg(vr + j) : 0.0;
+        const VT v = (j < pk) ? __ldcg(vr + j) : VT(0);
         if constexpr (KIND == tc::KIND_FP8) {
-          const double x = v * s_inv[j];
-          const __nv_fp8_storage_t h = __nv_cvt_double_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
-          const double hv = (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(h, __NV_E4M3)));
-          const __nv_fp8_storage_t l = __nv_cvt_double_to_fp8(x - hv, __NV_SATFINITE, __NV_E4M3);
+          const VT x = v * s_inv[j];
+          __nv_fp8_storage_t h, l;
+          if constexpr (kF32) {
+            h = __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+            const float hv = __half2float(__half(__nv_cvt_fp8_to_halfraw(h, __NV_E4M3)));
+            l = __nv_cvt_float_to_fp8(x - hv, __NV_SATFINITE, __NV_E4M3);
+          } else {
+            h = __nv_cvt_double_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+            const double hv = (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(h, __NV_E4M3)));
+            l = __nv_cvt_double_to_fp8(x - hv, __NV_SATFINITE, __NV_E4M3);
+          }
           uint8_t* o = reinterpret_cast<uint8_t*>(prm.lp_dq);
           o[(int64_t)j * ldk + i] = (uint8_t)h;
           o[(int64_t)(NP + j) * ldk + i] = (uint8_t)l;
@@ -1687,9 +1703,9 @@ __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t
       const int tr = (int)(i / tc::kBM);
       const int rr = (int)(i - (int64_t)tr * tc::kBM);
       const int c0 = s_rng[tr - tr0 - q0][0], c1 = s_rng[tr - tr0 - q0][1];
-      const double rs = prm.lp_row_scale ? (double)prm.lp_row_scale[i] : 1.0;
+      const VT rs = prm.lp_row_scale ? (VT)prm.lp_row_scale[i] : VT(1);
       for (int j0 = 0; j0 < pk; j0 += 4) {
-        double sv[4] = {0.0, 0.0, 0.0, 0.0};
+        VT sv[4] = {VT(0), VT(0), VT(0), VT(0)};
         for (int cc = c0; cc <= c1; ++cc) {
           if (some_empty && tc::unit_begin(U, G, cc + 1) <= tc::unit_begin(U, G, cc)) continue;
           const PartT* pr = part + ((size_t)(cc + tr) * tc::kBM + rr) * NP + j0;
@@ -1700,13 +1716,13 @@ __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t
               sv[0] += a.x; sv[1] += a.y; sv[2] += b.x; sv[3] += b.y;
             } else {
               const float4 a = __ldcg(reinterpret_cast<const float4*>(pr));
-              sv[0] += (double)a.x; sv[1] += (double)a.y;
-              sv[2] += (double)a.z; sv[3] += (double)a.w;
+              sv[0] += (VT)a.x; sv[1] += (VT)a.y;
+              sv[2] += (VT)a.z; sv[3] += (VT)a.w;
             }
           } else {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-              if (j0 + u < NP) sv[u] += (double)__ldcg(pr + u);
+              if (j0 + u < NP) sv[u] += (VT)__ldcg(pr + u);
           }
         }
         const int cnt = min(4, pk - j0);
@@ -1718,7 +1734,7 @@ __device__ bool lp_apass_epi(const Params& prm, const double* V, int pk, int64_t
               sv[u] *= rs * (double)__ldcg(&st->sigma[j]);
             } else {
               if (prm.lp_row_scale) sv[u] *= rs;
-              if constexpr (KIND == tc::KIND_FP8) sv[u] *= (double)__ldcg(&st->sigma[j]);
+              if constexpr (KIND == tc::KIND_FP8) sv[u] *= (VT)__ldcg(&st->sigma[j]);
             }
           }
         }
@@ -1920,16 +1936,107 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
           const double sg = th / de;
           double rho = 1.0 / sg;
           double* Z = prm.Z;
+          const int64_t cnt = (r1 - r0) * pk;
+          if constexpr (POL == POL_FP8) {
+            // FP8 operator: the recurrence runs in FP32 (d, S and Z as FP32
+            // blocks in the scratch area), and so do the operand split and
+            // the fixup; Z is widened to FP64 once, at the end.  The
+            // preconditioner needs only the accuracy of the quantised
+            // operator (E4M3, about 2^-4 relative with the row scales), and
+            // the FP32 rate is 64 times the FP64 rate on GB300.  The column
+            // maxima of each new d come from the update itself, as FP32 bit
+            // patterns (two buffers: one feeds the next pass while the other
+            // fills).
+            float* df = reinterpret_cast<float*>(prm.cheb_d);
+            float* sf = reinterpret_cast<float*>(prm.cheb_s);
+            float* zf = reinterpret_cast<float*>(prm.cheb_w);
+            __shared__ unsigned long long s_cf[2][P];
+            for (int j = tid; j < 2 * P; j += kThreads) (&s_cf[0][0])[j] = 0ull;
+            __syncthreads();
+            const float inv_th = (float)(1.0 / th);
+            for (int64_t idx = tid; idx < cnt; idx += kThreads) {
+              const int64_t o = (r0 + idx / pk) * p + idx % pk;
+              const float r = (float)ldcg(prm.V + o);
+              const float v = r * inv_th;
+              df[o] = v;
+              zf[o] = v;
+              sf[o] = r;
+              atomicMax(&s_cf[0][idx % pk], (unsigned long long)__float_as_uint(fabsf(v)));
+            }
+            __syncthreads();
+            // each step: W = A_lp d ; S -= W ; d = c1 d + c2 S ; Z += d, done
+            // on the fixup's entries as they are summed, four columns at a time
+            const bool vec4 = (p & 3) == 0;
+            int cmb = 0;
+            for (int k = 1; k < prm.cheb_steps; ++k) {
+              const double rn = 1.0 / (2.0 * sg - rho);
+              const float c1 = (float)(rn * rho), c2 = (float)(2.0 * rn / de);
+              unsigned long long* cm_next = s_cf[cmb ^ 1];
+              for (int j = tid; j < P; j += kThreads) cm_next[j] = 0ull;
+              __syncthreads();
+              const bool ok = lp_apass_epi<P, POL>(
+                  prm, static_cast<const float*>(df), pk, r0, r1, *L, &ss, &s_err, false,
+                  [&](int64_t i, int j0, const float (&w)[4], int cn) {
+                    const int64_t o = i * p + j0;
+                    float sv[4], dv[4], zv[4];
+                    if (vec4 && cn == 4) {
+                      const float4 s4 = *reinterpret_cast<const float4*>(sf + o);
+                      const float4 d4 = *reinterpret_cast<const float4*>(df + o);
+                      const float4 z4 = *reinterpret_cast<const float4*>(zf + o);
+                      sv[0] = s4.x; sv[1] = s4.y; sv[2] = s4.z; sv[3] = s4.w;
+                      dv[0] = d4.x; dv[1] = d4.y; dv[2] = d4.z; dv[3] = d4.w;
+                      zv[0] = z4.x; zv[1] = z4.y; zv[2] = z4.z; zv[3] = z4.w;
+                    } else {
+#pragma unroll
+                      for (int u = 0; u < 4; ++u)
+                        if (u < cn) {
+                          sv[u] = sf[o + u];
+                          dv[u] = df[o + u];
+                          zv[u] = zf[o + u];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                      if (u < cn) {
+                        sv[u] -= w[u];
+                        dv[u] = c1 * dv[u] + c2 * sv[u];
+                        zv[u] += dv[u];
+                        atomicMax(&cm_next[j0 + u],
+                                  (unsigned long long)__float_as_uint(fabsf(dv[u])));
+                      }
+                    }
+                    if (vec4 && cn == 4) {
+                      *reinterpret_cast<float4*>(sf + o) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+                      *reinterpret_cast<float4*>(df + o) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+                      *reinterpret_cast<float4*>(zf + o) = make_float4(zv[0], zv[1], zv[2], zv[3]);
+                    } else {
+#pragma unroll
+                      for (int u = 0; u < 4; ++u)
+                        if (u < cn) {
+                          sf[o + u] = sv[u];
+                          df[o + u] = dv[u];
+                          zf[o + u] = zv[u];
+                        }
+                    }
+                  },
+                  s_cf[cmb]);
+              if (!ok) return;
+              rho = rn;
+              cmb ^= 1;
+            }
+            for (int64_t idx = tid; idx < cnt; idx += kThreads) {
+              const int64_t o = (r0 + idx / pk) * p + idx % pk;
+              Z[o] = (double)zf[o];
+            }
+            return;
+          } else {
           double* d = prm.cheb_d;
           double* sr = prm.cheb_s;
-          // FP8: the column maxima of each new d come from the update itself
-          // (two buffers: one feeds the next pass while the other fills)
-          constexpr bool kMax = POL == POL_FP8;
+          constexpr bool kMax = false;
           __shared__ unsigned long long s_cm[2][P];
           if (kMax)
             for (int j = tid; j < 2 * P; j += kThreads) (&s_cm[0][0])[j] = 0ull;
           __syncthreads();
-          const int64_t cnt = (r1 - r0) * pk;
           for (int64_t idx = tid; idx < cnt; idx += kThreads) {
             const int64_t o = (r0 + idx / pk) * p + idx % pk;
             const double r = ldcg(prm.V + o);
@@ -2024,6 +2131,7 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
             conv = conv_next;
           }
           return;
+          }
         }
       }
     }
