@@ -109,7 +109,7 @@ typedef struct {
                                    CCG_MIXED_REFINE or CCG_MIXED_PRECOND      */
     int cheb_degree;            /* CCG_MIXED_PRECOND: products with the
                                    quantised A per preconditioner application;
-                                   0 = 36 (FP8), 32 (FP32) or 48 (BF16)      */
+                                   0 = 32 (FP8, FP32) or 48 (BF16)            */
     double cheb_ratio;          /* CCG_MIXED_PRECOND: lower end of the
                                    Chebyshev interval as a fraction of the
                                    upper end (a bound on the largest

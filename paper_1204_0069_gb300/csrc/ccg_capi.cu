@@ -293,7 +293,6 @@ int solve_impl(ccg_handle_s* h, int64_t n, const double* A, int64_t lda, const d
     // measured best on the precision workload: 32 products for FP8, 48 for BF16
     cp.cheb_steps = h->cfg.cheb_degree > 0 ? h->cfg.cheb_degree
                     : pre->format == CCG_LOWP_BF16 ? 48
-                    : pre->format == CCG_LOWP_FP8_E4M3 ? 36
                                                    : 32;
     const double ratio = h->cfg.cheb_ratio > 0.0 ? h->cfg.cheb_ratio : 1e-4;
     prm.precond = 1;
