@@ -2032,10 +2032,6 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
           } else {
           double* d = prm.cheb_d;
           double* sr = prm.cheb_s;
-          constexpr bool kMax = false;
-          __shared__ unsigned long long s_cm[2][P];
-          if (kMax)
-            for (int j = tid; j < 2 * P; j += kThreads) (&s_cm[0][0])[j] = 0ull;
           __syncthreads();
           for (int64_t idx = tid; idx < cnt; idx += kThreads) {
             const int64_t o = (r0 + idx / pk) * p + idx % pk;
@@ -2044,8 +2040,6 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
             d[o] = v;
             Z[o] = v;
             sr[o] = r;
-            if (kMax)
-              atomicMax(&s_cm[0][idx % pk], (unsigned long long)__double_as_longlong(fabs(v)));
           }
           __syncthreads();
           // each step: W = A_lp d ; S -= W ; d = c1 d + c2 S ; Z += d, the update
@@ -2055,16 +2049,10 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
           constexpr bool kConvInFixup = POL == POL_BF16 || POL == POL_TF32X3;
           const bool vec2 = (p & 1) == 0;
           bool conv = false;
-          int cmb = 0;
           for (int k = 1; k < prm.cheb_steps; ++k) {
             const double rn = 1.0 / (2.0 * sg - rho);
             const double c1 = rn * rho, c2 = 2.0 * rn / de;
             const bool conv_next = kConvInFixup && k + 1 < prm.cheb_steps;
-            unsigned long long* cm_next = s_cm[cmb ^ 1];
-            if (kMax) {
-              for (int j = tid; j < P; j += kThreads) cm_next[j] = 0ull;
-              __syncthreads();
-            }
             const bool ok = lp_apass_epi<P, POL>(
                 prm, d, pk, r0, r1, *L, &ss, &s_err, conv,
                 [&](int64_t i, int j0, const double (&w)[4], int cn) {
@@ -2097,9 +2085,6 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
                       zv[u] += dv[u];
                       if (conv_next)
                         lp_put<LpCfg<POL>::KIND, LpNP<P, POL>::value>(prm, j0 + u, i, dv[u]);
-                      if (kMax)
-                        atomicMax(&cm_next[j0 + u],
-                                  (unsigned long long)__double_as_longlong(fabs(dv[u])));
                     }
                   }
                   if (vec2 && cn == 4) {
@@ -2118,11 +2103,9 @@ __device__ __forceinline__ void solve_body(const Params& prm, double* smem, LpCt
                         Z[o + u] = zv[u];
                       }
                   }
-                },
-                kMax ? s_cm[cmb] : nullptr);
+                });
             if (!ok) return;
             rho = rn;
-            cmb ^= 1;
             if (conv_next) {
               // the operand rows of every CTA are complete before the next pass
               asm volatile("fence.proxy.async.global;" ::: "memory");
