@@ -55,6 +55,38 @@ def test_config_defaults(libpath):
     cfg = ccg.Config()
     ccg.lib().ccg_config_init(ctypes.byref(cfg))
     assert cfg.rank_tol == 1e-12 and cfg.x0_spread == 1.0 and cfg.residual_replacement == 1
+    assert cfg.precision == ccg.FP64 and cfg.mixed_method == ccg.MIXED_AUTO
+    assert cfg.cheb_degree == 0 and cfg.cheb_ratio == 0.0 and cfg.batch_autotune == 1
+
+
+@pytest.mark.parametrize("field,value", [
+    ("rank_tol", 0.0), ("rank_tol", -1.0), ("barrier_timeout_ms", 0.0),
+    ("precision", 5), ("precision", -1), ("max_ctas", -1), ("inner_tol", -1e-3),
+    ("max_outer", -1), ("explicit_residual", 2), ("batch_autotune", 2),
+    ("mixed_method", 3), ("cheb_degree", -1), ("cheb_degree", 1025),
+    ("cheb_ratio", 1.0), ("cheb_ratio", -0.5)])
+def test_create_rejects_each_invalid_field_before_cuda(libpath, field, value):
+    """ccg_create validates the whole configuration before its first CUDA
+    call, so every out-of-range field gives CCG_ERR_INVALID on any host."""
+    from paper_1204_0069_gb300 import ccg
+    L = ccg.lib()
+    cfg = ccg.Config()
+    L.ccg_config_init(ctypes.byref(cfg))
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    assert L.ccg_create(ctypes.byref(h), ctypes.byref(cfg)) == -1
+    assert not h.value
+
+
+def test_explicit_residual_needs_fp64(libpath):
+    from paper_1204_0069_gb300 import ccg
+    L = ccg.lib()
+    cfg = ccg.Config()
+    L.ccg_config_init(ctypes.byref(cfg))
+    cfg.explicit_residual = 1
+    cfg.precision = ccg.FP64_SLICED
+    h = ctypes.c_void_p()
+    assert L.ccg_create(ctypes.byref(h), ctypes.byref(cfg)) == -1
 
 
 def test_invalid_arguments_rejected_before_any_device_work(libpath):
