@@ -418,7 +418,13 @@ int ccg_server_create(const ccg_server_config* cfg, ccg_server** out) {
   ccg_server_config c;
   if (cfg) c = *cfg;
   else ccg_server_config_init(&c);
-  if (c.workers < 1 || c.workers > 64 || !(c.budget_bytes > 0.0) || c.ctas_per_worker < 0)
+  // everything that does not depend on the device is checked before the
+  // first CUDA call
+  if (c.workers < 1 || c.workers > 64 || !(c.budget_bytes > 0.0) || c.ctas_per_worker < 0 ||
+      (c.precision != CCG_FP64 && c.precision != CCG_FP32_IR && c.precision != CCG_BF16_IR &&
+       c.precision != CCG_FP8_IR && c.precision != CCG_FP64_SLICED) ||
+      c.slots < 0 || c.max_n < 0 || c.max_p < 0 || c.max_p > ccg::kMaxP ||
+      (c.slots > 0 && c.precision != CCG_FP64))
     return CCG_ERR_INVALID;
   int sms = 0;
   if (cudaSetDevice(c.device) != cudaSuccess ||
@@ -426,9 +432,7 @@ int ccg_server_create(const ccg_server_config* cfg, ccg_server** out) {
     cudaGetLastError();
     return CCG_ERR_INVALID;
   }
-  if (c.slots < 0 || c.slots > sms || c.max_n < 0 || c.max_p < 0 || c.max_p > ccg::kMaxP ||
-      (c.slots > 0 && c.precision != CCG_FP64))
-    return CCG_ERR_INVALID;
+  if (c.slots > sms) return CCG_ERR_INVALID;
   ccg_server_s* s = new (std::nothrow) ccg_server_s();
   if (!s) return CCG_ERR_OOM;
   s->cfg = c;

@@ -97,3 +97,30 @@ def test_invalid_arguments_rejected_before_any_device_work(libpath):
     assert L.ccg_solve(None, 4, None, 4, None, None, 1, 1e-8, 10, None, ctypes.byref(r)) == -1
     assert L.ccg_destroy(None) == 0
     assert L.ccg_create(None, None) == -1
+
+
+@pytest.mark.parametrize("field,value", [
+    ("workers", 0), ("workers", 65), ("budget_bytes", 0.0), ("ctas_per_worker", -1),
+    ("precision", 7), ("slots", -1), ("max_n", -1), ("max_p", -1), ("max_p", 33)])
+def test_server_rejects_each_invalid_field_before_cuda(libpath, field, value):
+    """ccg_server_create checks every field that does not depend on the
+    device before its first CUDA call (CCG_ERR_INVALID on any host)."""
+    from paper_1204_0069_gb300 import ccg
+    L = ccg.lib()
+    cfg = ccg.ServerConfig()
+    L.ccg_server_config_init(ctypes.byref(cfg))
+    setattr(cfg, field, value)
+    srv = ctypes.c_void_p()
+    assert L.ccg_server_create(ctypes.byref(cfg), ctypes.byref(srv)) == -1
+    assert not srv.value
+
+
+def test_server_slots_serve_fp64_only(libpath):
+    from paper_1204_0069_gb300 import ccg
+    L = ccg.lib()
+    cfg = ccg.ServerConfig()
+    L.ccg_server_config_init(ctypes.byref(cfg))
+    cfg.slots = 8
+    cfg.precision = ccg.FP8_IR
+    srv = ctypes.c_void_p()
+    assert L.ccg_server_create(ctypes.byref(cfg), ctypes.byref(srv)) == -1
